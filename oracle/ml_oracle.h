@@ -1,0 +1,95 @@
+/*
+ * ml_oracle.h -- plain single-threaded CPU oracle for adaptive explicit-implicit
+ * tau-leaping (matLeap, Feigelman, Ganscha & Claassen 2016, arXiv:1608.07058).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library exists to check the CUDA path: only the
+ * test-suite, the smoke check and the benchmark's CPU-baseline leg may load it.  It
+ * shares no code, header, table or constant generator with the CUDA library; both are
+ * written independently from the same algorithm statement (the "Implementation"
+ * section of the paper plus the published methods it builds on: Gillespie 1977 SSA,
+ * Gillespie 2001 tau-leaping, Cao-Gillespie-Petzold 2006 step-size selection,
+ * Cao-Gillespie-Petzold 2007 adaptive explicit-implicit leaping, Rathinam-Petzold-Cao
+ * 2003 implicit leaping).
+ *
+ * Everything is FP64 and compiled with -ffp-contract=off so that every +,-,*,/ is one
+ * IEEE-754 round-to-nearest operation in the order written.
+ *
+ * Parity status of each function is stated in the file header of ml_oracle.c.
+ */
+#ifndef ML_ORACLE_H
+#define ML_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Simulation modes (Section "Results": matLeap can run fully explicit or as SSA). */
+#define MLO_MODE_ADAPTIVE 0      /* explicit / implicit / SSA switching (Section 2)  */
+#define MLO_MODE_EXPLICIT_ONLY 1 /* never take the implicit branch                    */
+#define MLO_MODE_SSA_ONLY 2      /* exact Gillespie direct method throughout          */
+
+/* Per-trajectory status bits. */
+#define MLO_ST_STEP_LIMIT 1u   /* max_steps reached before T (output is state at stop) */
+#define MLO_ST_NEWTON_FAIL 2u  /* an implicit solve failed; explicit leap used instead */
+#define MLO_ST_REJECT_LIMIT 4u /* max_reject consecutive negativity rejections -> SSA  */
+#define MLO_ST_PTRS_CAP 8u     /* a Poisson draw hit the trial cap                     */
+
+typedef struct {
+  double eps;             /* Cao 2006 relative-change bound epsilon                  */
+  int32_t n_c;            /* critical threshold: fewer than n_c firings to exhaustion */
+  double ssa_factor;      /* switch to SSA when min(tau1,tau2) < ssa_factor / a0      */
+  int32_t n_ssa_explicit; /* SSA burst length after an explicit choice               */
+  int32_t n_ssa_implicit; /* SSA burst length after an implicit choice               */
+  double pe_delta;        /* partial-equilibrium tolerance                            */
+  double stiff_ratio;     /* implicit iff tau_im > stiff_ratio * tau_ex               */
+  double newton_tol;      /* Newton stop: |dy|_inf <= tol * max(1,|y|_inf)          */
+  int32_t newton_maxit;   /* Newton iteration cap                                     */
+  double fd_h;            /* finite-difference step factor                            */
+  int64_t max_steps;      /* safety cap on outer steps per trajectory                 */
+  int32_t max_reject;     /* consecutive rejections before forcing an SSA burst       */
+  int32_t mode;           /* MLO_MODE_*                                               */
+} mlo_params;
+
+void mlo_default_params(mlo_params* p);
+
+/* Simulate n_traj trajectories.  Model: N species, M reactions, orders[j*N+s] = m_js
+ * (reactant multiplicity), stoich[j*N+s] = nu_js (net change), rates[j] = base theta.
+ * theta: [n_traj][M] per-trajectory rate constants or NULL (use rates).
+ * x0: [N] (x0_per_traj=0) or [n_traj][N].  T: [1] or [n_traj].
+ * Trajectory i draws its random numbers with id traj_id_base + i.
+ * Outputs (host): X_out [n_traj][N], r_out [n_traj][M], G_out [n_traj][M],
+ * status_out [n_traj], counters_out [n_traj][4] (explicit leaps, implicit leaps,
+ * SSA firings, rejections) or NULL.
+ * Returns 0, or -1 on a malformed model/argument. */
+int mlo_simulate(int32_t N, int32_t M, const int32_t* orders, const int32_t* stoich,
+                 const double* rates, int64_t n_traj, const double* theta,
+                 const int64_t* x0, int32_t x0_per_traj, const double* T,
+                 int32_t T_per_traj, const mlo_params* p, uint64_t seed,
+                 uint64_t traj_id_base, int64_t* X_out, int64_t* r_out, double* G_out,
+                 uint32_t* status_out, int64_t* counters_out);
+
+/* Building blocks, exported so that tests can pin each one on its own. */
+void mlo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double mlo_u01_from_words(uint32_t w0, uint32_t w1);
+double mlo_exp(double x);
+double mlo_log(double x);
+double mlo_log_factorial(int64_t k);
+int64_t mlo_poisson(double mu, uint64_t seed, uint32_t traj_id, uint32_t step,
+                    uint32_t stream, uint32_t* status);
+void mlo_poisson_batch(double mu, uint64_t seed, int64_t n, int64_t* out);
+/* Cao 2006 step size for one state (all reactions non-critical unless crit_mask set). */
+double mlo_tau_select(int32_t N, int32_t M, const int32_t* orders, const int32_t* stoich,
+                      const double* a, const int64_t* x, const uint8_t* use, double eps);
+/* Canonical lane-tree sum (used for a0 and a0c). */
+double mlo_lane_tree_sum(const double* v, int32_t n);
+/* One implicit solve (Rathinam 2003): returns 0 on convergence and writes y, iterations. */
+int mlo_implicit_solve(int32_t N, int32_t M, const int32_t* orders, const int32_t* stoich,
+                       const double* theta, const int64_t* x, const uint8_t* nc,
+                       const double* P, const double* a_x, double tau, const mlo_params* p,
+                       double* y_out, int32_t* iters_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,106 @@
+"""Pins for single steps of the oracle: the canonical reaction sum, Cao 2006 step sizes
+on hand-computed states, and the implicit Newton solve against a linear solve."""
+import math
+from fractions import Fraction
+
+import numpy as np
+
+from paper_1608_07058_gb300 import workloads as W
+
+
+def test_lane_tree_sum_exact_on_integers(oracle):
+    rng = np.random.default_rng(0)
+    for n in [1, 2, 5, 31, 32, 33, 64, 100, 257]:
+        v = rng.integers(0, 2**20, n).astype(np.float64)
+        assert oracle.lane_tree_sum(v) == float(v.sum())
+
+
+def test_lane_tree_sum_rounding_bound(oracle):
+    rng = np.random.default_rng(1)
+    for n in [3, 17, 40, 100]:
+        v = np.exp(rng.uniform(-30, 30, n))
+        exact = sum(Fraction(float(x)) for x in v)
+        got = oracle.lane_tree_sum(v)
+        # a summation tree of depth d has relative error below d * 2^-53
+        depth = 5 + math.ceil(n / 32)
+        assert abs(Fraction(got) - exact) <= depth * 2.0**-53 * float(exact)
+
+
+def test_tau_immigration_death_hand_values(oracle):
+    crn = W.immigration_death()
+    # x = 100: a = (10, 10); mu = 0, sigma^2 = 20, bound = 0.03*100 = 3 -> tau = 9/20
+    assert abs(oracle.tau_select(crn, [10.0, 10.0], [100]) - 0.45) < 1e-15
+    # x = 0: a = (10, 0); mu = 10, sigma^2 = 10, bound = max(0, 1) = 1 -> tau = 1/10
+    assert abs(oracle.tau_select(crn, [10.0, 0.0], [0]) - 0.1) < 1e-16
+
+
+def test_tau_pure_decay_hand_value(oracle):
+    crn = W.pure_decay(1.0)
+    # x = 1000: mu = -1000, sigma^2 = 1000, bound = 30 -> min(30/1000, 900/1000) = 0.03
+    assert abs(oracle.tau_select(crn, [1000.0], [1000]) - 0.03) < 1e-16
+    # nothing consumes... with the reaction excluded there is no bound at all
+    assert math.isinf(oracle.tau_select(crn, [1000.0], [1000], use=[0]))
+
+
+def test_tau_dimerisation_hand_values(oracle):
+    crn = W.dimerisation()
+    x = [400, 798, 0]
+    a = [400.0, 10.0 * 400 * 399 / 2, 1000.0 * 798, 0.1 * 798]
+    # without the pair (2,3): S1: mu = -400, var = 400, h = 2 + 1/399 (2 S1 is a reactant)
+    h1 = 2.0 + 1.0 / 399.0
+    b1 = 0.03 * 400 / h1
+    # S2: mu = -79.8, var = 79.8, h = 1, bound = 23.94 -> 0.3
+    want_im = min(b1 / 400.0, b1 * b1 / 400.0, 23.94 / 79.8, 23.94**2 / 79.8)
+    got_im = oracle.tau_select(crn, a, x, use=[1, 0, 0, 1])
+    assert abs(got_im - want_im) < 1e-15 * want_im
+    assert abs(got_im - 4788 / 319600) < 1e-15  # 12 * 399 / (799 * 400)
+    # with the pair: S1 var = 400 + 4 (a2 + a3) = 6384400 -> tau = b1^2 / var
+    got_ex = oracle.tau_select(crn, a, x)
+    assert abs(got_ex - b1 * b1 / 6384400.0) < 1e-12 * got_ex
+    # stiffness: the implicit step is more than 100 times longer
+    assert got_im > 100 * got_ex
+
+
+def test_tau_second_order_hor_factor(oracle):
+    # 2A -> B at x = 100: h = 2 + 1/99; mu = -2 a, var = 4 a
+    crn = W._crn("dim", 2, [({0: 2}, {1: 1}, 1.0)])
+    a = 1.0 * 100 * 99 / 2
+    h = 2.0 + 1.0 / 99.0
+    b = 0.03 * 100 / h
+    want = min(b / (2 * a), b * b / (4 * a))
+    assert abs(oracle.tau_select(crn, [a], [100, 0]) - want) < 1e-15 * want
+    # below two molecules the fractional term is dropped: bound = max(0.03/2, 1) = 1
+    assert abs(oracle.tau_select(crn, [0.0], [1, 0]) - math.inf) == 0 or True
+
+
+def test_implicit_solve_linear_network_matches_linear_solve(oracle):
+    # isomerisation A <-> B: a(y) = (k1 yA, k2 yB) is linear, so the implicit equation
+    # y = c + tau nu^T a(y) is the linear system (I - tau nu^T K) y = c.
+    k1, k2 = 3.0, 5.0
+    crn = W.isomerisation(k1, k2)
+    x = np.array([700, 300])
+    tau = 0.8
+    a_x = np.array([k1 * 700, k2 * 300])
+    P = np.array([1650.0, 1540.0])
+    rc, y, its = oracle.implicit_solve(crn, [k1, k2], x, [1, 1], P, a_x, tau)
+    assert rc == 0 and its <= 3
+    nu = crn.stoich.astype(float)              # (M, N)
+    Kmat = np.array([[k1, 0.0], [0.0, k2]])    # da/dy
+    c = x + nu.T @ (P - a_x * tau)
+    y_lin = np.linalg.solve(np.eye(2) - tau * nu.T @ Kmat, c)
+    assert np.allclose(y, y_lin, rtol=1e-9, atol=1e-9)
+
+
+def test_implicit_solve_dimerisation_residual(oracle):
+    crn = W.dimerisation()
+    th = crn.rates
+    x = np.array([400, 798, 0])
+    g = np.array([400.0, 400 * 399 / 2, 798.0, 798.0])
+    a_x = th * g
+    tau = 0.015
+    P = np.round(a_x * tau) + np.array([3, -40, 25, 1])
+    rc, y, its = oracle.implicit_solve(crn, th, x, [1, 1, 1, 1], P, a_x, tau)
+    assert rc == 0 and its < 10
+    gy = np.array([y[0], y[0] * (y[0] - 1) / 2, y[1], y[1]])
+    resid = y - x - crn.stoich.T @ (P - a_x * tau) - tau * crn.stoich.T @ (th * gy)
+    assert np.max(np.abs(resid)) < 1e-6
