@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark: ensembles of adaptive tau-leaping trajectories on one GPU per rank.
+
+Workload (default): the stiff decaying-dimerising network (3 species, 4 reactions,
+S1 -> 0, 2 S1 -> S2, S2 -> 2 S1, S2 -> S3 with rates 1, 10, 1000, 0.1), x0 = (400, 798, 0),
+T = 0.2, eps = 0.03, n_c = 10, 100,000 trajectories per GPU (weak scaling: rank k simulates
+trajectory ids [k B, (k+1) B)).
+
+A step is one simulate call over the whole batch.  Two forms are timed:
+  batched  fast precision (FP32 propensities, FP64 t/G/Newton), persistent refill
+           kernel launched from a CUDA graph, autotuned shape  -> the headline `value`;
+  plain    reference precision (FP64 everywhere), one launch, one thread per trajectory.
+Inputs are resident in HBM when timing starts; a 256 MB buffer is written between steps to
+flush L2.  `e2e` times the host-buffer entry point (pinned host memory, copies inside).
+`cpu_baseline` times the CPU oracle on the host, single-threaded, on a bounded sample.
+`--impl reference` times only the oracle (the reference arm for this method).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "trajectories/s & leap-steps/s, batched vs plain launch, at oracle-matched stats"
+MAX_STEPS = 1_000_000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--n-traj", type=int, default=None)
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0,
+                    help="target CPU seconds for the oracle baseline sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--ncu", action="store_true",
+                    help="skip the CPU leg, autotune, e2e and clocks (for profiler runs)")
+    return ap.parse_args()
+
+
+def workload_name(w):
+    return (f"{w.name}: {w.crn.n_species} species x {w.crn.n_reactions} reactions, "
+            f"{w.n_traj} trajectories per GPU, T={'per-trajectory' if w.T.size > 1 else float(w.T[0])}, "
+            f"eps={w.eps}, n_c={w.n_c}")
+
+
+# ---------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------
+# algorithmic work model (arithmetic the method needs per event)
+# ---------------------------------------------------------------------------------
+PHILOX_OPS = 70      # 10 rounds x (2 wide multiplies, 3 xors, 2 key adds)
+UNIFORM_OPS = 3
+LOG_OPS = 15
+POISSON_INV_OPS = 40  # exp, ~3 search steps of 3 ops, uniform
+POISSON_PTRS_OPS = 110
+
+
+def work_model(crn):
+    import numpy as np
+    o, nu = crn.orders, crn.stoich
+    N, M = crn.n_species, crn.n_reactions
+    fac = {1: 1, 2: 4, 3: 6}
+    props = int(sum(sum(fac[int(m)] for m in row if m > 0) + 1 for row in o))
+    nnz = int((nu != 0).sum())
+    nreact = int((o.sum(0) > 0).sum())
+    ssa = props + (M - 1) + PHILOX_OPS + 2 * UNIFORM_OPS + LOG_OPS + 1 + 2 * M + 2 * (nnz / M) + 2 * M + 1
+    leap = (2 * props + (M - 1) + 2 * int((nu < 0).sum()) + 4 * nnz + 7 * nreact
+            + M * (PHILOX_OPS + POISSON_INV_OPS) + nnz + 3 * M + M)
+    newton_it = (N + 1) * props + 2 * nnz * (N + 1) + (2 * N ** 3) // 3 + 4 * N * N + 6 * N
+    implicit = leap + 3 * newton_it + 4 * M
+    reject = leap - props - nnz
+    return {"explicit_leap": leap, "implicit_leap": implicit, "ssa_firing": ssa,
+            "rejected_leap": reject, "assumed_newton_iterations": 3}
+
+
+def ops_from_counts(model_ops, counts):
+    return (counts[0] * model_ops["explicit_leap"] + counts[1] * model_ops["implicit_leap"]
+            + counts[2] * model_ops["ssa_firing"] + counts[3] * model_ops["rejected_leap"])
+
+
+# ---------------------------------------------------------------------------------
+# reference arm and CPU baseline: the oracle on the host
+# ---------------------------------------------------------------------------------
+def oracle_rate(w, budget_s, seed=0, first_id=0):
+    """Time the oracle on a prefix sample of the workload sized to ~budget_s.
+    Returns (trajectories/s, n_sample, seconds, outputs)."""
+    from oracle import oracle as O
+    params = O.Params(max_steps=MAX_STEPS)
+    n = min(w.n_traj, 200)
+    t0 = time.perf_counter()
+    O.simulate(w.crn, n, w.x0[:n] if w.x0.ndim == 2 else w.x0, w.T[:n] if w.T.size > 1 else w.T,
+               None if w.theta is None else w.theta[:n], params=params, seed=seed, traj_id_base=first_id)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    n = int(min(w.n_traj, max(n, n * budget_s / dt)))
+    xs = w.x0[:n] if w.x0.ndim == 2 else w.x0
+    Ts = w.T[:n] if w.T.size > 1 else w.T
+    th = None if w.theta is None else w.theta[:n]
+    t0 = time.perf_counter()
+    out = O.simulate(w.crn, n, xs, Ts, th, params=params, seed=seed, traj_id_base=first_id)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, out
+
+
+def run_reference(args):
+    from paper_1608_07058_gb300 import workloads as W
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = W.config(args.config, n_traj=args.n_traj)
+    per_step_budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    rates, n_used = [], 0
+    for s in range(args.warmup + args.steps):
+        rate, n, dt, _ = oracle_rate(w, per_step_budget, seed=s)
+        if s >= args.warmup:
+            rates.append(rate)
+            n_used = n
+    value = statistics.mean(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "trajectories/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * w.n_traj / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(w)},
+            "cpu_baseline": {"value": value, "unit": "trajectories/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {n_used} trajectory ids of the workload per step, "
+                                       f"single-threaded C oracle (FP64 reference algorithm)"},
+            "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1608_07058_gb300 import matleap as ml
+    from paper_1608_07058_gb300 import workloads as W
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor(v, dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return t.cpu().numpy()
+
+    w = W.config(args.config, n_traj=args.n_traj)
+    B = w.n_traj
+    id_base = rank * B
+    model = ml.model_from_crn(w.crn)
+    x0 = torch.as_tensor(w.x0, device=dev)
+    T = torch.as_tensor(w.T, device=dev)
+    theta = None if w.theta is None else torch.as_tensor(w.theta, device=dev)
+    stream = torch.cuda.current_stream()
+
+    fast = ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32, form=ml.ML_FORM_PERSISTENT,
+                                use_graph=1, max_steps=MAX_STEPS)
+    if not args.ncu:
+        best = ml.ml_autotune(model, B, x0, T, theta, params=fast, n_sample=min(B, 32768))
+        fast.shape, fast.block_size, fast.ctas_per_sm = best.shape, best.block_size, best.ctas_per_sm
+    plain = ml.ml_default_params(precision=ml.ML_PREC_REF_FP64, form=ml.ML_FORM_PLAIN,
+                                 max_steps=MAX_STEPS, block_size=128)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
+
+    def timed(params, seed0):
+        out = {"X": torch.empty((B, model.N), dtype=torch.int64, device=dev),
+               "r": torch.empty((B, model.M), dtype=torch.int64, device=dev),
+               "G": torch.empty((B, model.M), dtype=torch.float64, device=dev),
+               "status": torch.empty((B,), dtype=torch.int32, device=dev),
+               "counters": torch.empty((B, 4), dtype=torch.int64, device=dev)}
+        for s in range(args.warmup):
+            ml.ml_simulate(model, B, x0, T, theta, params=params, seed=seed0 + s,
+                           traj_id_base=id_base, out=out)
+        torch.cuda.synchronize()
+        acc = torch.zeros(4, dtype=torch.int64, device=dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        launches = 0
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            ml.ml_simulate(model, B, x0, T, theta, params=params, seed=seed0 + args.warmup + k,
+                           traj_id_base=id_base, out=out)
+            evs[k][1].record(stream)
+            launches += ml.ml_model_last_launch_count(model)
+            acc += out["counters"].sum(0)
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - t0
+        ms = [a.elapsed_time(b) for a, b in evs]
+        bad = int((out["status"] & ~(ml.ML_ST_NEWTON_FAIL | ml.ML_ST_PTRS_CAP)).ne(0).sum().item())
+        return {"ms": ms, "mean_ms": statistics.mean(ms), "counts": acc.cpu().numpy(),
+                "wall_s": wall, "launches": launches, "last_out": out,
+                "last_seed": seed0 + args.warmup + args.steps - 1, "bad_status": bad}
+
+    clocks = ClockSampler(local)
+    if not args.ncu:
+        clocks.start()
+    res_fast = timed(fast, 1000)
+    clk = clocks.stop() if not args.ncu else None
+    res_plain = None if args.no_plain else timed(plain, 5000)
+
+    ms_fast = max_over_ranks(res_fast["mean_ms"])
+    counts_fast = sum_over_ranks(res_fast["counts"].astype(np.float64)) / args.steps
+    value = world * B / (ms_fast / 1e3)
+    leap_steps = float(counts_fast[0] + counts_fast[1] + counts_fast[2])
+    line = {"metric": METRIC, "value": value, "unit": "trajectories/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_fast,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": workload_name(w), "form": "persistent refill kernel, CUDA graph, autotuned",
+                       "precision": "FP32 propensities/tau/Poisson, FP64 t/G/Newton",
+                       "shape": {"shape": "thread" if fast.shape == ml.ML_SHAPE_THREAD else ("warp" if fast.shape == ml.ML_SHAPE_WARP else "auto"),
+                                 "block_size": fast.block_size, "ctas_per_sm": fast.ctas_per_sm},
+                       "l2": "flushed between steps (256 MB write)"},
+            "leap_steps_per_s": leap_steps / (ms_fast / 1e3),
+            "mode_mix_per_step": {"explicit_leaps": float(counts_fast[0]), "implicit_leaps": float(counts_fast[1]),
+                                  "ssa_firings": float(counts_fast[2]), "rejected_leaps": float(counts_fast[3])},
+            "gpu_launches": int(res_fast["launches"])}
+    if res_plain is not None:
+        ms_plain = max_over_ranks(res_plain["mean_ms"])
+        counts_plain = sum_over_ranks(res_plain["counts"].astype(np.float64)) / args.steps
+        line["plain_fp64"] = {"value": world * B / (ms_plain / 1e3), "unit": "trajectories/s",
+                              "ms_per_step": ms_plain,
+                              "leap_steps_per_s": float(counts_plain[:3].sum()) / (ms_plain / 1e3),
+                              "form": "one launch, one thread per trajectory, FP64 reference precision"}
+        line["batched_vs_plain"] = line["value"] / line["plain_fp64"]["value"]
+        line["gpu_launches_plain"] = int(res_plain["launches"])
+
+    # roofline of the headline kernel: algorithmic operations against the issue rate
+    ops_model = work_model(w.crn)
+    ops_per_launch = ops_from_counts(ops_model, counts_fast / world)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peak_clock = 2070.0
+    peak = sms * 128 * peak_clock * 1e6 / 1e12   # Tops/s: SMs x 4 schedulers x 32 lanes x clock
+    achieved = ops_per_launch / (ms_fast / 1e3) / 1e12
+    line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "peak_basis": f"{sms} SMs x 128 lanes x {peak_clock:.0f} MHz (issue rate, one op per lane per clock)",
+                        "work_model_ops_per_event": ops_model}
+    if clk:
+        line["clocks"] = clk
+        line["roofline"]["frac_at_measured_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 / 1e12)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    if not args.ncu:
+        pin = lambda a: torch.as_tensor(a).pin_memory()
+        hx0, hT = pin(w.x0), pin(w.T)
+        hth = None if w.theta is None else pin(w.theta)
+        hout = {"X": torch.empty((B, model.N), dtype=torch.int64).pin_memory(),
+                "r": torch.empty((B, model.M), dtype=torch.int64).pin_memory(),
+                "G": torch.empty((B, model.M), dtype=torch.float64).pin_memory(),
+                "status": torch.empty((B,), dtype=torch.int32).pin_memory(),
+                "counters": torch.empty((B, 4), dtype=torch.int64).pin_memory()}
+        for s in range(args.warmup):
+            ml.ml_simulate_host(model, B, hx0, hT, hth, params=fast, seed=s, traj_id_base=id_base,
+                                out=hout, stream=stream)
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            ml.ml_simulate_host(model, B, hx0, hT, hth, params=fast, seed=100 + k,
+                                traj_id_base=id_base, out=hout, stream=stream)
+        barrier()
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+        h2d = hx0.numel() * 8 + hT.numel() * 8 + (0 if hth is None else hth.numel() * 8)
+        d2h = sum(v.numel() * v.element_size() for v in hout.values())
+        line["e2e"] = {"value": world * B / e2e_s, "unit": "trajectories/s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "path": "ml_simulate_host: pinned host inputs -> device -> simulate -> host"}
+
+    # CPU oracle baseline and oracle-matched statistics (rank 0, N = 1 only for the baseline)
+    if rank == 0 and not args.no_cpu and not args.ncu:
+        rate, n, dt, oout = oracle_rate(w, args.cpu_budget_s, seed=res_fast["last_seed"], first_id=id_base)
+        if world == 1:
+            line["cpu_baseline"] = {"value": rate, "unit": "trajectories/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"first {n} trajectory ids of the workload ({dt:.1f} s), "
+                                              f"single-threaded C oracle, FP64 reference algorithm"}
+        from tests import stats_util
+        g = {k: v[:n].cpu().numpy() for k, v in res_fast["last_out"].items()}
+        rows = stats_util.compare(g, oout)
+        line["parity"] = {"fast_vs_oracle": stats_util.summary(rows), "n_compared": n,
+                          "bad_status": res_fast["bad_status"]}
+    if rank == 0:
+        print(json.dumps(line, default=float), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * matleap.h -- C ABI of the GB300 (sm_103a) ensemble simulator for adaptive
+ * explicit-implicit tau-leaping of mass-action chemical reaction networks
+ * (matLeap, Feigelman, Ganscha & Claassen, arXiv:1608.07058).
+ *
+ * What one trajectory computes (paper, Section 1 "Background" and Section 2
+ * "Implementation"): starting from x0 at t = 0 it advances the network to the horizon T
+ * by the adaptive method -- Cao-Gillespie-Petzold (2006) epsilon-bounded leaps,
+ * critical reactions (fewer than n_c firings from exhaustion fire at most once per
+ * leap), implicit leaps (Rathinam-Petzold-Cao 2003) when leaving out reaction pairs in
+ * partial equilibrium gives a much longer leap (Cao-Gillespie-Petzold 2007), and the
+ * paper's switch to exact SSA bursts when the wait to the next critical firing, or the
+ * leap itself, is comparable to the wait to the next reaction -- and returns
+ *   X(T)  the final state,
+ *   r_j   the number of firings of reaction j,
+ *   G_j   the integral over [0, T] of g_j(X_s), where a_j(x) = theta_j g_j(x) and
+ *         g_j(x) = prod_s C(x_s, m_js) (trapezoid on leaps, exact under SSA),
+ * which are the sufficient statistics of the Gamma(alpha_j + r_j, beta_j + G_j)
+ * posterior of each rate constant (Section 1).
+ *
+ * Conventions for every entry point:
+ *  - Return value: ML_OK (0) or a negative ML_ERR_* code.  Nothing aborts or throws.
+ *    ml_last_error() returns a thread-local message for the last failure.
+ *  - Argument errors are detected synchronously on the host, before any launch.
+ *  - Device pointers must be device (or managed) memory of the current device; a host
+ *    pointer where a device pointer is expected is rejected with ML_ERR_ARG.
+ *  - The caller owns every buffer it passes; the library owns ml_model / ml_server
+ *    objects and their internal device tables.
+ *  - Per-trajectory anomalies are reported in status_out (ML_ST_* bits), never through
+ *    the return code.
+ *  - Random numbers: Philox4x32-10 keyed by (seed) with counter (trajectory id, step,
+ *    stream, block), trajectory id = traj_id_base + i, so results do not depend on
+ *    batch composition, launch shape or sharding.
+ */
+#ifndef MATLEAP_H
+#define MATLEAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------------------ */
+#define ML_OK 0
+#define ML_ERR_ARG (-1)     /* malformed model or argument                           */
+#define ML_ERR_OOM (-2)     /* device or host allocation failed                      */
+#define ML_ERR_CUDA (-3)    /* a CUDA runtime call failed (message in ml_last_error) */
+#define ML_ERR_TIMEOUT (-4) /* a bounded wait ran out                                */
+#define ML_ERR_BUSY (-5)    /* the server cannot admit the request now               */
+#define ML_ERR_UNSUPPORTED (-6) /* no kernel variant for this model size/precision   */
+
+/* ---- per-trajectory status bits (status_out) --------------------------------------- */
+#define ML_ST_STEP_LIMIT 1u    /* max_steps reached before T; X is the state at the stop */
+#define ML_ST_NEWTON_FAIL 2u   /* an implicit solve failed; an explicit leap was taken   */
+#define ML_ST_REJECT_LIMIT 4u  /* max_reject rejections in a row forced an SSA burst     */
+#define ML_ST_PTRS_CAP 8u      /* a Poisson draw hit its trial cap                       */
+#define ML_ST_BAD_INPUT 16u    /* negative x0 or theta, or a NaN: trajectory not run     */
+#define ML_ST_STAGE_TIMEOUT 32u /* model staging wait ran out; plain loads were used     */
+
+/* ---- modes (Section 3: matLeap can also run fully explicit or as SSA) -------------- */
+#define ML_MODE_ADAPTIVE 0      /* explicit / implicit / SSA switching                  */
+#define ML_MODE_EXPLICIT_ONLY 1 /* never take the implicit branch                       */
+#define ML_MODE_SSA_ONLY 2      /* exact Gillespie direct method throughout             */
+
+/* ---- arithmetic ------------------------------------------------------------------- */
+#define ML_PREC_REF_FP64 0  /* FP64 everywhere, fixed operation order, no FMA: per
+                               trajectory bit-identical to the CPU reference            */
+#define ML_PREC_FAST_FP32 1 /* FP32 propensities, step sizes and Poisson means; FP64
+                               time, G accumulation and implicit Newton solve          */
+
+/* ---- launch forms ----------------------------------------------------------------- */
+#define ML_FORM_PLAIN 0      /* one launch, one thread (or warp) per trajectory         */
+#define ML_FORM_PERSISTENT 1 /* resident CTAs refill finished slots from a device work
+                                queue; optionally replayed from a CUDA graph           */
+
+/* ---- kernel shapes ---------------------------------------------------------------- */
+#define ML_SHAPE_AUTO 0   /* thread per trajectory when the model fits, else warp     */
+#define ML_SHAPE_THREAD 1 /* one trajectory per thread (N <= 8, M <= 16)               */
+#define ML_SHAPE_WARP 2   /* one trajectory per warp (N <= 64, M <= 128)               */
+
+typedef struct ml_model ml_model;
+
+/* Control parameters.  Defaults from ml_default_params():
+ * eps 0.03, n_c 10, ssa_factor 10, n_ssa_explicit 100, n_ssa_implicit 10,
+ * pe_delta 0.05, stiff_ratio 100, newton_tol 1e-10, newton_maxit 20, fd_h 1e-7,
+ * max_steps 1e8, max_reject 64, mode ADAPTIVE, precision REF_FP64, form PLAIN,
+ * shape AUTO, block_size 0 (tuned or default), ctas_per_sm 0, use_graph 0. */
+typedef struct {
+  double eps;             /* Cao 2006 bound on the relative change of each reactant    */
+  int32_t n_c;            /* critical threshold (Section 2)                            */
+  double ssa_factor;      /* SSA burst when min(tau1, tau2) < ssa_factor / a0          */
+  int32_t n_ssa_explicit; /* burst length after an explicit choice                     */
+  int32_t n_ssa_implicit; /* burst length after an implicit choice                     */
+  double pe_delta;        /* pair in partial equilibrium: |a_j - a_k| <= pe_delta min  */
+  double stiff_ratio;     /* implicit iff tau_im > stiff_ratio * tau_ex                */
+  double newton_tol;      /* Newton stop: |dy|_inf <= newton_tol * max(1, |y|_inf)     */
+  int32_t newton_maxit;   /* Newton iteration cap                                      */
+  double fd_h;            /* forward-difference step factor for the Jacobian           */
+  int64_t max_steps;      /* outer-step cap per trajectory                             */
+  int32_t max_reject;     /* rejections in a row before an SSA burst is forced         */
+  int32_t mode;           /* ML_MODE_*                                                 */
+  int32_t precision;      /* ML_PREC_*                                                 */
+  int32_t form;           /* ML_FORM_*                                                 */
+  int32_t shape;          /* ML_SHAPE_*                                                */
+  int32_t block_size;     /* threads per CTA; 0 = autotuned value or default           */
+  int32_t ctas_per_sm;    /* persistent form: resident CTAs per SM; 0 = tuned/default  */
+  int32_t use_graph;      /* persistent form: launch through a cached CUDA graph       */
+} ml_sim_params;
+
+/* Fills *p with the defaults above.  Returns ML_ERR_ARG if p is NULL. */
+int ml_default_params(ml_sim_params* p);
+
+/* Thread-local message describing the last failed call on this thread ("" if none). */
+const char* ml_last_error(void);
+
+/* Creates a model (paper Section 1: mass-action network, a_j = theta_j g_j(X)).
+ *   n_species N >= 1, n_reactions M >= 1 (N <= 64, M <= 128).
+ *   reactant_orders [M][N] row-major host array: m_js >= 0, sum_s m_js <= 3.
+ *   net_stoich      [M][N] row-major host array: nu_js >= -m_js, |nu_js| <= 127.
+ *   rates           [M] host array: default rate constants, finite and >= 0.
+ * The arrays are copied; device tables are uploaded lazily on first use per device.
+ * Reversible pairs (reaction k the chemical reverse of reaction j, both with a
+ * reactant) are found here.  Errors: ML_ERR_ARG, ML_ERR_OOM. */
+int ml_model_create(int32_t n_species, int32_t n_reactions, const int32_t* reactant_orders,
+                    const int32_t* net_stoich, const double* rates, ml_model** out);
+
+/* Frees the model and its device tables and cached graphs.  NULL is a no-op.  The
+ * caller must make sure no launch that uses the model is still running. */
+int ml_model_destroy(ml_model* model);
+
+/* Number of reversible pairs found in the model (>= 0), or ML_ERR_ARG. */
+int ml_model_num_pairs(const ml_model* model);
+
+/* Simulates n_traj independent trajectories on the current device, asynchronously on
+ * cuda_stream (a cudaStream_t; NULL = legacy default stream).
+ *   theta  [n_traj][M] device FP64 per-trajectory rate constants, or NULL for the
+ *          model's rates.
+ *   x0     device int64: [N] (x0_per_traj = 0, shared) or [n_traj][N].
+ *   T      device FP64: [1] (T_per_traj = 0) or [n_traj] horizons.
+ *   p      control parameters (NULL = defaults).
+ *   seed, traj_id_base: trajectory i uses id traj_id_base + i; ids must stay below 2^32.
+ *   X_out  [n_traj][N] int64, r_out [n_traj][M] int64, G_out [n_traj][M] FP64,
+ *   status_out [n_traj] uint32, counters_out [n_traj][4] int64 or NULL (accepted
+ *          explicit leaps, implicit leaps, SSA firings, rejected leaps) -- all device.
+ * n_traj == 0 returns ML_OK without launching.  Errors: ML_ERR_ARG (bad sizes, host
+ * pointers, parameters out of range), ML_ERR_UNSUPPORTED (no variant for this size),
+ * ML_ERR_CUDA (launch failure), ML_ERR_OOM (internal scratch). */
+int ml_simulate(const ml_model* model, int64_t n_traj, const double* theta,
+                const int64_t* x0, int32_t x0_per_traj, const double* T,
+                int32_t T_per_traj, const ml_sim_params* p, uint64_t seed,
+                uint64_t traj_id_base, int64_t* X_out, int64_t* r_out, double* G_out,
+                uint32_t* status_out, int64_t* counters_out, void* cuda_stream);
+
+/* Same as ml_simulate with HOST buffers (same shapes): copies inputs to device
+ * workspace owned by the model, runs, copies results back and synchronizes the stream
+ * before returning.  Pinned host memory makes the copies asynchronous DMA.
+ * Not reentrant for one model: concurrent calls on the same model must be serialized
+ * by the caller (ML_ERR_BUSY is returned if a call is already running). */
+int ml_simulate_host(ml_model* model, int64_t n_traj, const double* theta,
+                     const int64_t* x0, int32_t x0_per_traj, const double* T,
+                     int32_t T_per_traj, const ml_sim_params* p, uint64_t seed,
+                     uint64_t traj_id_base, int64_t* X_out, int64_t* r_out, double* G_out,
+                     uint32_t* status_out, int64_t* counters_out, void* cuda_stream);
+
+/* Project autotuner: times candidate kernel shapes (trajectory per thread or per warp,
+ * threads per CTA, resident CTAs per SM) on the first min(n_traj, n_sample)
+ * trajectories of the given inputs, with p's mode/precision/form, and stores the
+ * fastest in the model (used when a later call passes block_size = 0) and in *best.
+ * Synchronizes cuda_stream.  Uses internal scratch outputs. */
+int ml_autotune(ml_model* model, int64_t n_traj, const double* theta, const int64_t* x0,
+                int32_t x0_per_traj, const double* T, int32_t T_per_traj,
+                const ml_sim_params* p, uint64_t seed, int64_t n_sample,
+                ml_sim_params* best, void* cuda_stream);
+
+/* Number of kernel launches the last ml_simulate/ml_simulate_host call on this model
+ * issued (a graph replay counts its kernel nodes), or ML_ERR_ARG. */
+int64_t ml_model_last_launch_count(const ml_model* model);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

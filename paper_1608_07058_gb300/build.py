@@ -1,0 +1,83 @@
+"""Build the CUDA library libmatleap.so in-tree for sm_103a.
+
+Each kernel variant is its own translation unit (precision x table capacity), compiled
+in parallel; the reference-precision units get -fmad=false so that no multiply-add is
+contracted.  Objects go to _build/ next to this file; the library next to this file.
+"""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libmatleap.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+N_THREAD_VARIANTS = 4
+
+
+def _nvcc():
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
+        if c and os.path.exists(c):
+            return c
+    raise RuntimeError("nvcc not found: the CUDA library cannot be built")
+
+
+def _units():
+    u = []
+    for fast in (0, 1):
+        for v in range(N_THREAD_VARIANTS):
+            u.append(("kern_thread.cu", f"kt_{'fast' if fast else 'ref'}_{v}.o",
+                      [f"-DML_FAST={fast}", f"-DML_VARIANT={v}"] + ([] if fast else ["-fmad=false"])))
+        u.append(("kern_warp.cu", f"kw_{'fast' if fast else 'ref'}.o",
+                  [f"-DML_FAST={fast}"] + ([] if fast else ["-fmad=false"])))
+    u.append(("api.cu", "api.o", []))
+    return u
+
+
+def _sources():
+    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "matleap.h")]
+
+
+def up_to_date():
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(s) <= t for s in _sources())
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and up_to_date():
+        return LIB
+    nvcc = _nvcc()
+    os.makedirs(BUILD, exist_ok=True)
+    common = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+              "-I", INCLUDE, "-I", CSRC]
+    jobs = []
+    for src, obj, flags in _units():
+        cmd = common + flags + ["-c", os.path.join(CSRC, src), "-o", os.path.join(BUILD, obj)]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        jobs.append(cmd)
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
+    for cmd, res in zip(jobs, results):
+        if verbose and res.stderr:
+            sys.stderr.write(res.stderr)
+        if res.returncode != 0:
+            raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{res.stderr}")
+    objs = [os.path.join(BUILD, o) for _, o, _ in _units()]
+    tmp = LIB + ".tmp"
+    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    res = subprocess.run(link, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"link failed: {' '.join(link)}\n{res.stderr}")
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

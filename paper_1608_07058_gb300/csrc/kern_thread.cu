@@ -1,0 +1,35 @@
+// One thread-per-trajectory kernel variant, selected at compile time:
+//   ML_FAST = 0: reference precision (compile with -fmad=false), 1: fast precision;
+//   ML_VARIANT: index into the (species, reactions) capacity table.
+#include "thread_core.cuh"
+
+#ifndef ML_VARIANT
+#error "ML_VARIANT must be defined"
+#endif
+#define ML_CAT_(a, b, c) a##b##_##c
+#define ML_CAT(a, b, c) ML_CAT_(a, b, c)
+
+namespace mlk {
+#if ML_FAST
+using Prec = PrecFast;
+#define ML_PNAME fast
+#else
+using Prec = PrecRef;
+#define ML_PNAME ref
+#endif
+
+namespace {
+constexpr int kNM = kThreadN[ML_VARIANT];
+constexpr int kMM = kThreadM[ML_VARIANT];
+cudaError_t launch(const void* dm, const SimArgs& a, int grid, int block, size_t smem,
+                   cudaStream_t s) {
+  k_thread<kNM, kMM, Prec><<<grid, block, smem, s>>>(
+      static_cast<const ThreadModel<kNM, kMM>*>(dm), a);
+  return cudaGetLastError();
+}
+}  // namespace
+
+KernelEntry ML_CAT(thread_entry_, ML_PNAME, ML_VARIANT)() {
+  return KernelEntry{&launch, reinterpret_cast<const void*>(&k_thread<kNM, kMM, Prec>)};
+}
+}  // namespace mlk

@@ -1,0 +1,132 @@
+// Internal declarations shared by the CUDA library's translation units (host API and
+// kernels).  Nothing here is visible through include/matleap.h.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace mlk {
+
+// Thread-per-trajectory variants, (species, reactions) capacities.  A model is run on
+// the smallest variant that holds it; padded species start at 0 and are touched by no
+// reaction, padded reactions have no reactants, no effect and rate 0.
+constexpr int kThreadVariants = 4;
+constexpr int kThreadN[kThreadVariants] = {1, 3, 3, 8};
+constexpr int kThreadM[kThreadVariants] = {2, 4, 6, 16};
+
+// Warp-per-trajectory capacities.
+constexpr int kWarpMaxN = 64;
+constexpr int kWarpMaxM = 128;
+
+// Highest-order-reaction flags per species (Cao 2006): which (reaction order, molecules
+// of this species) combinations occur among the reactions that consume it.
+enum : uint8_t {
+  kHorO1 = 1,     // first order
+  kHorO2M1 = 2,   // S + S'
+  kHorO2M2 = 4,   // 2S
+  kHorO3M1 = 8,   // S + S' + S''
+  kHorO3M2 = 16,  // 2S + S'
+  kHorO3M3 = 32,  // 3S
+};
+
+// Model tables for the thread-per-trajectory kernels, one fixed layout per variant.
+// Staged into shared memory at kernel start by one bulk copy.
+template <int NM, int MM>
+struct alignas(16) ThreadModel {
+  double rates[MM];
+  int8_t ord[MM][NM];   // m_js
+  int8_t nu[MM][NM];    // nu_js
+  int8_t partner[MM];   // for the lower reaction of a reversible pair: the other; else -1
+  uint8_t isreact[NM];  // species consumed by some reaction
+  uint8_t hor[NM];      // kHor* flags
+  int32_t n_pairs;
+  int32_t N, M;         // real sizes
+};
+
+template <int NM, int MM>
+__host__ __device__ constexpr size_t thread_model_bytes() {
+  return (sizeof(ThreadModel<NM, MM>) + 15) / 16 * 16;
+}
+
+// Model tables for the warp-per-trajectory kernels (compact sparse lists).
+struct alignas(16) WarpModel {
+  double rates[kWarpMaxM];
+  int32_t N, M, n_pairs, nnz;
+  // reactants of reaction j: up to 3 (species, multiplicity), increasing species
+  int8_t rsp[kWarpMaxM][3];
+  int8_t rmul[kWarpMaxM][3];
+  int8_t nreact[kWarpMaxM];
+  int8_t partner[kWarpMaxM];      // as in ThreadModel
+  uint8_t isreact[kWarpMaxN];
+  uint8_t hor[kWarpMaxN];
+  // nonzero net changes of reaction j: rx_ptr[j] .. rx_ptr[j+1]
+  int16_t rx_ptr[kWarpMaxM + 1];
+  // reactions changing species s, increasing j: sp_ptr[s] .. sp_ptr[s+1]
+  int16_t sp_ptr[kWarpMaxN + 1];
+  int16_t pad0;
+  // entries (filled up to nnz): per-reaction lists then per-species lists
+  int8_t rx_s[kWarpMaxM * 8];
+  int8_t rx_nu[kWarpMaxM * 8];
+  int16_t sp_j[kWarpMaxM * 8];
+  int8_t sp_nu[kWarpMaxM * 8];
+};
+
+// Everything a simulation kernel needs besides the model tables.
+struct SimArgs {
+  int64_t n_traj;
+  const double* theta;  // [n_traj][M] or null
+  const int64_t* x0;    // [N] or [n_traj][N]
+  const double* T;      // [1] or [n_traj]
+  int32_t x0_per, T_per;
+  int32_t N, M;         // real sizes (I/O strides, random-stream numbering)
+  uint64_t seed;
+  uint64_t id_base;
+  int64_t* X;
+  int64_t* r;
+  double* G;
+  uint32_t* status;
+  int64_t* counters;    // or null
+  // control parameters
+  double eps;
+  double ssa_factor;
+  double pe_delta;
+  double stiff_ratio;
+  double newton_tol;
+  double fd_h;
+  int64_t max_steps;
+  int32_t n_c;
+  int32_t n_ssa_ex;
+  int32_t n_ssa_im;
+  int32_t newton_maxit;
+  int32_t max_reject;
+  int32_t mode;
+  // persistent form: next unclaimed trajectory (zeroed before each launch)
+  unsigned long long* queue;
+};
+
+// One compiled kernel variant: its launcher and its function pointer (for occupancy
+// queries and CUDA-graph kernel nodes).  Every kernel takes (model tables, SimArgs).
+using LaunchFn = cudaError_t (*)(const void* dmodel, const SimArgs& a, int grid, int block,
+                                 size_t smem, cudaStream_t s);
+struct KernelEntry {
+  LaunchFn launch;
+  const void* kernel;
+};
+
+// Thread-per-trajectory variants (kern_thread.cu, one object per precision x variant).
+KernelEntry thread_entry_ref_0();
+KernelEntry thread_entry_ref_1();
+KernelEntry thread_entry_ref_2();
+KernelEntry thread_entry_ref_3();
+KernelEntry thread_entry_fast_0();
+KernelEntry thread_entry_fast_1();
+KernelEntry thread_entry_fast_2();
+KernelEntry thread_entry_fast_3();
+// Warp-per-trajectory kernels (kern_warp.cu, one object per precision).
+KernelEntry warp_entry_ref();
+KernelEntry warp_entry_fast();
+// Dynamic shared memory of the warp kernel for a CTA of `warps` warps.
+size_t warp_smem_bytes(int warps);
+
+}  // namespace mlk

@@ -1,0 +1,679 @@
+// One trajectory per thread: the adaptive explicit-implicit tau-leaping loop for small
+// networks (N <= 8 species, M <= 16 reactions), templated on the table capacities
+// (NM, MM) and on the arithmetic (P = PrecRef: FP64, fixed operation order, bitwise
+// reproducible; P = PrecFast: FP32 propensities/step sizes/Poisson means, FP64 time, G
+// and Newton).  All per-trajectory arrays are indexed with compile-time indices only so
+// that they live in registers.
+//
+// Steps (paper Section 2, with the published methods it names):
+//   propensities a_j = theta_j g_j(x), a0                       (Section 1)
+//   critical reactions: a_j > 0 and min_s floor(x_s/|nu_js|) < n_c
+//   tau_ex: Cao 2006 bound on mean and variance of each reactant's change
+//   partial-equilibrium pairs, tau_im without them, implicit iff tau_im >> tau_ex
+//   tau2 ~ Exp(a0c); SSA burst if min(tau1, tau2) < ssa_factor / a0
+//   explicit Poisson leap or implicit Newton leap (Rathinam 2003); one critical firing
+//   negativity check (halve tau1 and retry); commit x, r, G (trapezoid) and t.
+#pragma once
+#include <cstdint>
+
+#include "dev_common.cuh"
+#include "ml_internal.h"
+#include "matleap.h"
+
+namespace mlk {
+
+// Canonical sum over reactions for a0 and a0c: element j on lane j (j < 32); lanes
+// combined pairwise at xor distances 16, 8, 4, 2, 1; lane 0's value.  Written for one
+// thread holding all elements (MM <= 32), with empty lanes holding 0.
+template <int MM, class R>
+__device__ __forceinline__ R lane_tree_sum(const R (&v)[MM]) {
+  static_assert(MM <= 32, "thread variant holds at most 32 reactions");
+  R lane[32];
+#pragma unroll
+  for (int l = 0; l < 32; ++l) lane[l] = (l < MM) ? v[l] : R(0);
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+#pragma unroll
+    for (int l = 0; l < d; ++l) lane[l] = lane[l] + lane[l + d];
+  }
+  return lane[0];
+}
+
+// C(v, m) for m = 1, 2, 3 on a real argument, in this operation order.
+template <class R>
+__device__ __forceinline__ R comb_factor(R v, int m) {
+  if (m == 1) return v;
+  if (m == 2) return (v * (v - R(1))) * R(0.5);
+  return ((v * (v - R(1))) * (v - R(2))) / R(6);
+}
+
+// Highest-order-reaction factor h_s (Cao 2006) from the species' flags and count.
+template <class R>
+__device__ __forceinline__ R hor_factor(uint8_t f, long long x) {
+  const R xd = (R)x;
+  R h = R(0);
+  if (f & kHorO1) h = h < R(1) ? R(1) : h;
+  if (f & kHorO2M1) h = h < R(2) ? R(2) : h;
+  if (f & kHorO2M2) {
+    const R v = x >= 2 ? R(2) + R(1) / (xd - R(1)) : R(2);
+    h = h < v ? v : h;
+  }
+  if (f & kHorO3M1) h = h < R(3) ? R(3) : h;
+  if (f & kHorO3M2) {
+    const R v = x >= 2 ? R(1.5) * (R(2) + R(1) / (xd - R(1))) : R(3);
+    h = h < v ? v : h;
+  }
+  if (f & kHorO3M3) {
+    const R v = x >= 3 ? (R(3) + R(1) / (xd - R(1))) + R(2) / (xd - R(2)) : R(3);
+    h = h < v ? v : h;
+  }
+  return h;
+}
+
+struct PrecRef {
+  using R = double;
+  static constexpr bool kRef = true;
+  __device__ static __forceinline__ R u(const Words4& w, int k) {
+    return k == 0 ? u01_f64(w.w0, w.w1) : u01_f64(w.w2, w.w3);
+  }
+  __device__ static __forceinline__ R log(R x) { return refmath::log_ref(x); }
+  __device__ static __forceinline__ R exp(R x) { return refmath::exp_ref(x); }
+  __device__ static __forceinline__ R lfact(long long k) {
+    return refmath::log_factorial_ref(k);
+  }
+  __device__ static __forceinline__ R sqrt(R x) { return ::sqrt(x); }
+  __device__ static __forceinline__ R inf() {
+    return __longlong_as_double(0x7ff0000000000000LL);
+  }
+};
+
+struct PrecFast {
+  using R = float;
+  static constexpr bool kRef = false;
+  __device__ static __forceinline__ R u(const Words4& w, int k) {
+    return k == 0 ? u01_f32(w.w0) : u01_f32(w.w2);
+  }
+  __device__ static __forceinline__ R log(R x) { return __logf(x); }
+  __device__ static __forceinline__ R exp(R x) { return __expf(x); }
+  __device__ static __forceinline__ R lfact(long long k) {
+    return lgammaf((float)k + 1.0f);
+  }
+  __device__ static __forceinline__ R sqrt(R x) { return sqrtf(x); }
+  __device__ static __forceinline__ R inf() { return __int_as_float(0x7f800000); }
+};
+
+// FP64 PTRS with library functions, used by the fast path for very large means where
+// FP32 cannot hold the integer count exactly.
+struct PrecWide {
+  using R = double;
+  static constexpr bool kRef = false;
+  __device__ static __forceinline__ R u(const Words4& w, int k) {
+    return k == 0 ? u01_f64(w.w0, w.w1) : u01_f64(w.w2, w.w3);
+  }
+  __device__ static __forceinline__ R log(R x) { return ::log(x); }
+  __device__ static __forceinline__ R exp(R x) { return ::exp(x); }
+  __device__ static __forceinline__ R lfact(long long k) { return ::lgamma((double)k + 1.0); }
+  __device__ static __forceinline__ R sqrt(R x) { return ::sqrt(x); }
+  __device__ static __forceinline__ R inf() {
+    return __longlong_as_double(0x7ff0000000000000LL);
+  }
+};
+
+constexpr int kPtrsMaxTrials = 256;
+
+// PTRS: Hoermann (1993), transformed rejection with squeeze, for mean mu >= 10.  Trial b
+// uses block b of the stream: U from the first uniform, V from the second.
+template <class P>
+__device__ __noinline__ long long poisson_ptrs(typename P::R mu, uint32_t k0, uint32_t k1,
+                                               uint32_t id, uint32_t step, uint32_t stream,
+                                               uint32_t& status) {
+  using R = typename P::R;
+  const R slam = P::sqrt(mu);
+  const R loglam = P::log(mu);
+  const R b = R(0.931) + R(2.53) * slam;
+  const R a = R(-0.059) + R(0.02483) * b;
+  const R inv_alpha = R(1.1239) + R(1.1328) / (b - R(3.4));
+  const R v_r = R(0.9277) - R(3.6224) / (b - R(2));
+  for (uint32_t trial = 0; trial < (uint32_t)kPtrsMaxTrials; ++trial) {
+    const Words4 w = philox_block(k0, k1, id, step, stream, trial);
+    const R U = P::u(w, 0) - R(0.5);
+    const R V = P::u(w, 1);
+    const R us = R(0.5) - fabs(U);
+    const R kd = floor((((R(2) * a) / us + b) * U + mu) + R(0.43));
+    if (us >= R(0.07) && V <= v_r) return (long long)kd;
+    if (kd < R(0) || (us < R(0.013) && V > us)) continue;
+    const R lhs = (P::log(V) + P::log(inv_alpha)) - P::log(a / (us * us) + b);
+    const R rhs = (-mu + kd * loglam) - P::lfact((long long)kd);
+    if (lhs <= rhs) return (long long)kd;
+  }
+  status |= ML_ST_PTRS_CAP;
+  return (long long)floor(mu + R(0.5));
+}
+
+// Poisson(mu): 0 for mu <= 0 (no draw); inversion by sequential search below 10; PTRS.
+template <class P>
+__device__ __forceinline__ long long poisson_draw(typename P::R mu, uint32_t k0, uint32_t k1,
+                                                  uint32_t id, uint32_t step, uint32_t stream,
+                                                  uint32_t& status) {
+  using R = typename P::R;
+  if (!(mu > R(0))) return 0;
+  if (mu < R(10)) {
+    const Words4 w = philox_block(k0, k1, id, step, stream, 0);
+    const R u = P::u(w, 0);
+    R p = P::exp(-mu);
+    R F = p;
+    long long k = 0;
+    while (u > F) {
+      k = k + 1;
+      p = p * (mu / (R)k);
+      if (p == R(0)) break;
+      F = F + p;
+    }
+    return k;
+  }
+  if (!P::kRef && mu > R(4.0e6)) {
+    return poisson_ptrs<PrecWide>((double)mu, k0, k1, id, step, stream, status);
+  }
+  return poisson_ptrs<P>(mu, k0, k1, id, step, stream, status);
+}
+
+template <int NM, int MM, class P>
+struct ThreadTraj {
+  using R = typename P::R;
+  using Model = ThreadModel<NM, MM>;
+
+  // g_j at an integer state (0 when some x_s < m_js), product in increasing s.
+  __device__ static __forceinline__ R g_int(const Model& md, int j, const long long (&x)[NM]) {
+    R v = R(1);
+    bool zero = false;
+#pragma unroll
+    for (int s = 0; s < NM; ++s) {
+      const int m = md.ord[j][s];
+      if (m != 0) {
+        if (x[s] < m) zero = true;
+        else v = v * comb_factor<R>((R)x[s], m);
+      }
+    }
+    return zero ? R(0) : v;
+  }
+
+  // g_j at a real state (implicit solve), FP64 always.
+  __device__ static __forceinline__ double g_real(const Model& md, int j,
+                                                  const double (&y)[NM]) {
+    double v = 1.0;
+#pragma unroll
+    for (int s = 0; s < NM; ++s) {
+      const int m = md.ord[j][s];
+      if (m != 0) v = v * comb_factor<double>(y[s], m);
+    }
+    return v;
+  }
+
+  __device__ static __forceinline__ void eval_props(const Model& md, const long long (&x)[NM],
+                                                    const R (&th)[MM], R (&g)[MM], R (&a)[MM]) {
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      g[j] = g_int(md, j, x);
+      a[j] = th[j] * g[j];
+    }
+  }
+
+  // Cao 2006 step size over reactions in `use`: per reactant species,
+  // mu = sum nu a, var = sum nu^2 a (increasing j, nonzero nu), bound = max(eps x/h, 1),
+  // tau_s = min(bound/|mu|, bound^2/var); the minimum over species.
+  __device__ static __forceinline__ R tau_select(const Model& md, const R (&a)[MM],
+                                                 const long long (&x)[NM], uint32_t use, R eps) {
+    R tau = P::inf();
+#pragma unroll
+    for (int s = 0; s < NM; ++s) {
+      if (md.isreact[s]) {
+        R mu = R(0), var = R(0);
+#pragma unroll
+        for (int j = 0; j < MM; ++j) {
+          const int v = md.nu[j][s];
+          if (((use >> j) & 1u) && v != 0) {
+            mu = mu + (R)v * a[j];
+            var = var + (R)(v * v) * a[j];
+          }
+        }
+        const R h = hor_factor<R>(md.hor[s], x[s]);
+        R bound = (eps * (R)x[s]) / h;
+        if (bound < R(1)) bound = R(1);
+        const R t1 = bound / fabs(mu);
+        const R t2 = (bound * bound) / var;
+        const R ts = t1 < t2 ? t1 : t2;
+        if (ts < tau) tau = ts;
+      }
+    }
+    return tau;
+  }
+
+  // Implicit leap (Rathinam 2003): solve y = c + tau sum_j nu_j a_j(y) over the
+  // non-critical reactions by Newton with a forward-difference Jacobian, Gaussian
+  // elimination with partial pivoting and column-oriented back substitution.
+  // Returns 0 converged, 1 not converged, 2 singular.
+  __device__ static int implicit_solve(const Model& md, const R (&th)[MM],
+                                       const long long (&x)[NM], uint32_t nc,
+                                       const long long (&Pk)[MM], const R (&a)[MM],
+                                       double tau, double tol, int maxit, double fd_h,
+                                       double (&y)[NM]) {
+    double c[NM];
+#pragma unroll
+    for (int s = 0; s < NM; ++s) {
+      double acc = (double)x[s];
+#pragma unroll
+      for (int j = 0; j < MM; ++j) {
+        const int v = md.nu[j][s];
+        if (((nc >> j) & 1u) && v != 0)
+          acc = acc + (double)v * ((double)Pk[j] - (double)a[j] * tau);
+      }
+      c[s] = acc;
+      y[s] = (double)x[s];
+    }
+    for (int it = 0; it < maxit; ++it) {
+      double ay[MM];
+#pragma unroll
+      for (int j = 0; j < MM; ++j) ay[j] = (double)th[j] * g_real(md, j, y);
+      double A[NM][NM], b[NM];
+#pragma unroll
+      for (int s = 0; s < NM; ++s) {
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < MM; ++j) {
+          const int v = md.nu[j][s];
+          if (((nc >> j) & 1u) && v != 0) acc = acc + (double)v * ay[j];
+        }
+        b[s] = -((y[s] - c[s]) - tau * acc);
+      }
+#pragma unroll
+      for (int q = 0; q < NM; ++q) {
+        const double aq = fabs(y[q]);
+        const double h = fd_h * (aq > 1.0 ? aq : 1.0);
+        double yq[NM];
+#pragma unroll
+        for (int s = 0; s < NM; ++s) yq[s] = y[s];
+        yq[q] = y[q] + h;
+        const double he = yq[q] - y[q];
+        double Dq[MM];
+#pragma unroll
+        for (int j = 0; j < MM; ++j)
+          Dq[j] = (((nc >> j) & 1u) && md.ord[j][q] != 0)
+                      ? ((double)th[j] * g_real(md, j, yq) - ay[j]) / he
+                      : 0.0;
+#pragma unroll
+        for (int s = 0; s < NM; ++s) {
+          double acc = 0.0;
+#pragma unroll
+          for (int j = 0; j < MM; ++j) {
+            const int v = md.nu[j][s];
+            if (((nc >> j) & 1u) && v != 0 && md.ord[j][q] != 0)
+              acc = acc + (double)v * Dq[j];
+          }
+          A[s][q] = (s == q ? 1.0 : 0.0) - tau * acc;
+        }
+      }
+      // elimination with partial pivoting (row swaps by compile-time selects)
+#pragma unroll
+      for (int k = 0; k < NM; ++k) {
+        int piv = k;
+        double best = fabs(A[k][k]);
+#pragma unroll
+        for (int i = k + 1; i < NM; ++i) {
+          if (fabs(A[i][k]) > best) {
+            best = fabs(A[i][k]);
+            piv = i;
+          }
+        }
+        if (best == 0.0) return 2;
+#pragma unroll
+        for (int i = k + 1; i < NM; ++i) {
+          if (i == piv) {
+#pragma unroll
+            for (int cc = 0; cc < NM; ++cc) {
+              const double tmp = A[k][cc];
+              A[k][cc] = A[i][cc];
+              A[i][cc] = tmp;
+            }
+            const double tb = b[k];
+            b[k] = b[i];
+            b[i] = tb;
+          }
+        }
+#pragma unroll
+        for (int i = k + 1; i < NM; ++i) {
+          const double l = A[i][k] / A[k][k];
+#pragma unroll
+          for (int cc = k + 1; cc < NM; ++cc) A[i][cc] = A[i][cc] - l * A[k][cc];
+          b[i] = b[i] - l * b[k];
+        }
+      }
+      double d[NM];
+#pragma unroll
+      for (int i = NM - 1; i >= 0; --i) {
+        d[i] = b[i] / A[i][i];
+#pragma unroll
+        for (int rr = 0; rr < i; ++rr) b[rr] = b[rr] - A[rr][i] * d[i];
+      }
+      double dmax = 0.0, ymax = 0.0;
+#pragma unroll
+      for (int s = 0; s < NM; ++s) {
+        y[s] = y[s] + d[s];
+        if (fabs(d[s]) > dmax) dmax = fabs(d[s]);
+        if (fabs(y[s]) > ymax) ymax = fabs(y[s]);
+      }
+      if (dmax <= tol * (ymax > 1.0 ? ymax : 1.0)) return 0;
+    }
+    return 1;
+  }
+
+  // The whole trajectory.
+  __device__ static void run(const Model& md, const SimArgs& A, long long i) {
+    const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
+    const uint32_t id = (uint32_t)(A.id_base + (unsigned long long)i);
+    const uint32_t Mr = (uint32_t)A.M;  // stream numbering uses the real M
+    uint32_t status = 0;
+
+    R th[MM];
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      double v = 0.0;
+      if (j < A.M) v = A.theta ? A.theta[i * A.M + j] : md.rates[j];
+      if (!(v >= 0.0)) bad = true;
+      th[j] = (R)v;
+    }
+    long long x[NM];
+    const int64_t* x0 = A.x0_per ? A.x0 + i * A.N : A.x0;
+#pragma unroll
+    for (int s = 0; s < NM; ++s) {
+      x[s] = s < A.N ? x0[s] : 0;
+      if (x[s] < 0) bad = true;
+    }
+    const double T = A.T_per ? A.T[i] : A.T[0];
+    long long r[MM];
+    double G[MM];
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      r[j] = 0;
+      G[j] = 0.0;
+    }
+    long long cnt[4] = {0, 0, 0, 0};
+    double t = 0.0;
+    uint32_t step = 0;
+    int reject_run = 0;
+    if (bad) {
+      status |= ML_ST_BAD_INPUT;
+      t = T;
+    }
+    if (T != T) t = 0.0;  // NaN horizon: the loop below never runs
+
+    R g[MM], a[MM];
+
+    // SSA burst (Gillespie 1977 direct method): at most n_max firings at outer step
+    // `step`; g, a, a0 are current on entry.
+    auto ssa_burst = [&](int n_max, R a0) {
+      for (int b = 0; b < n_max; ++b) {
+        if (b > 0) {
+          eval_props(md, x, th, g, a);
+          a0 = lane_tree_sum<MM, R>(a);
+        }
+        if (a0 == R(0)) {
+          const double rem = T - t;
+#pragma unroll
+          for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)g[j] * rem;
+          t = T;
+          return;
+        }
+        const Words4 w = philox_block(k0, k1, id, step, Mr + 2u, (uint32_t)b);
+        const R u1 = P::u(w, 0);
+        const R u2 = P::u(w, 1);
+        const R dt = -P::log(u1) / a0;
+        const double tn = t + (double)dt;
+        if (tn > T) {
+          const double rem = T - t;
+#pragma unroll
+          for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)g[j] * rem;
+          t = T;
+          return;
+        }
+#pragma unroll
+        for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)g[j] * (double)dt;
+        t = tn;
+        const R target = u2 * a0;
+        R acc = R(0);
+        int pick = -1, last = -1;
+#pragma unroll
+        for (int j = 0; j < MM; ++j) {
+          if (a[j] > R(0)) last = j;
+          acc = acc + a[j];
+          if (pick < 0 && target < acc) pick = j;
+        }
+        if (pick < 0) pick = last;
+#pragma unroll
+        for (int s = 0; s < NM; ++s) x[s] += md.nu[pick][s];
+#pragma unroll
+        for (int j = 0; j < MM; ++j) r[j] += (j == pick) ? 1 : 0;
+        cnt[2] += 1;
+      }
+    };
+
+    const R eps = (R)A.eps;
+    for (;;) {
+      if (!(t < T)) break;
+      if ((long long)step >= A.max_steps) {
+        status |= ML_ST_STEP_LIMIT;
+        break;
+      }
+      eval_props(md, x, th, g, a);
+      const R a0 = lane_tree_sum<MM, R>(a);
+      if (a0 == R(0)) {
+        const double rem = T - t;
+#pragma unroll
+        for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)g[j] * rem;
+        t = T;
+        break;
+      }
+      int burst = 0;  // > 0: run an SSA burst of this many firings after the attempts
+      if (A.mode == ML_MODE_SSA_ONLY) burst = A.n_ssa_ex;
+      else {
+      // critical reactions
+      uint32_t nc = 0;
+      R ac[MM];
+#pragma unroll
+      for (int j = 0; j < MM; ++j) {
+        bool crit = false;
+        if (a[j] > R(0)) {
+          long long L = -1;
+#pragma unroll
+          for (int s = 0; s < NM; ++s) {
+            const int v = md.nu[j][s];
+            if (v < 0) {
+              const long long l = (v == -1) ? x[s] : x[s] / (long long)(-v);
+              if (L < 0 || l < L) L = l;
+            }
+          }
+          crit = (L >= 0 && L < (long long)A.n_c);
+        }
+        if (!crit) nc |= 1u << j;
+        ac[j] = crit ? a[j] : R(0);
+      }
+      const R a0c = lane_tree_sum<MM, R>(ac);
+      const R tau_ex = tau_select(md, a, x, nc, eps);
+      // partial equilibrium and the implicit step size
+      bool implicit = false;
+      R tau1 = tau_ex;
+      if (A.mode == ML_MODE_ADAPTIVE && md.n_pairs > 0) {
+        uint32_t pe = 0;
+#pragma unroll
+        for (int j = 0; j < MM; ++j) {
+          const int k = md.partner[j];
+          if (k >= 0 && ((nc >> j) & 1u) && ((nc >> k) & 1u)) {
+            R ak = R(0);
+#pragma unroll
+            for (int kk = 0; kk < MM; ++kk)
+              if (kk == k) ak = a[kk];
+            const R lo = a[j] < ak ? a[j] : ak;
+            if (fabs(a[j] - ak) <= (R)A.pe_delta * lo) pe |= (1u << j) | (1u << k);
+          }
+        }
+        if (pe != 0) {
+          const R tau_im = tau_select(md, a, x, nc & ~pe, eps);
+          if (tau_im > (R)A.stiff_ratio * tau_ex) {
+            implicit = true;
+            tau1 = tau_im;
+          }
+        }
+      }
+      // attempt loop
+      for (;;) {
+        if (reject_run >= A.max_reject) {
+          status |= ML_ST_REJECT_LIMIT;
+          burst = A.n_ssa_ex;
+          break;
+        }
+        R tau2 = P::inf();
+        if (a0c > R(0)) {
+          const Words4 w = philox_block(k0, k1, id, step, Mr, 0u);
+          tau2 = -P::log(P::u(w, 0)) / a0c;
+        }
+        const R tmin = tau1 < tau2 ? tau1 : tau2;
+        if (tmin < (R)A.ssa_factor / a0) {
+          burst = implicit ? A.n_ssa_im : A.n_ssa_ex;
+          break;
+        }
+        const double rem = T - t;
+        R tau = tau1;
+        if (tau2 < tau) tau = tau2;
+        bool at_horizon = false;
+        if ((R)rem <= tau) {
+          tau = (R)rem;
+          at_horizon = true;
+        }
+        const bool crit_fire = (tau2 <= tau1) && (tau2 <= (R)rem);
+        long long K[MM];
+#pragma unroll
+        for (int j = 0; j < MM; ++j) K[j] = 0;
+        if (crit_fire) {
+          const Words4 w = philox_block(k0, k1, id, step, Mr + 1u, 0u);
+          const R target = P::u(w, 0) * a0c;
+          R acc = R(0);
+          int pick = -1, last = -1;
+#pragma unroll
+          for (int j = 0; j < MM; ++j) {
+            if (ac[j] > R(0)) last = j;
+            acc = acc + ac[j];
+            if (pick < 0 && target < acc) pick = j;
+          }
+          if (pick < 0) pick = last;
+#pragma unroll
+          for (int j = 0; j < MM; ++j) K[j] = (j == pick) ? 1 : 0;
+        }
+        const bool implicit_step = implicit && tau > tau_ex;
+        // Poisson firings of the non-critical reactions (explicit counts, or the noise
+        // term P_j of the implicit equation)
+#pragma unroll
+        for (int j = 0; j < MM; ++j)
+          if ((nc >> j) & 1u)
+            K[j] = poisson_draw<P>(a[j] * tau, k0, k1, id, step, (uint32_t)j, status);
+        if (implicit_step) {
+          double y[NM];
+          const double taud = (double)tau;
+          const int rc = implicit_solve(md, th, x, nc, K, a, taud, A.newton_tol,
+                                        A.newton_maxit, A.fd_h, y);
+          if (rc != 0) {
+            status |= ML_ST_NEWTON_FAIL;
+            implicit = false;
+            tau1 = tau_ex;
+            step++;
+            continue;
+          }
+#pragma unroll
+          for (int j = 0; j < MM; ++j) {
+            if ((nc >> j) & 1u) {
+              const double ayj = (double)th[j] * g_real(md, j, y);
+              const double v = (ayj * taud + (double)K[j]) - (double)a[j] * taud;
+              const double rv = round(v);
+              K[j] = rv > 0.0 ? (long long)rv : 0;
+            }
+          }
+        }
+        long long xn[NM];
+        bool negative = false;
+#pragma unroll
+        for (int s = 0; s < NM; ++s) {
+          long long v = x[s];
+#pragma unroll
+          for (int j = 0; j < MM; ++j) v += (long long)md.nu[j][s] * K[j];
+          xn[s] = v;
+          if (v < 0) negative = true;
+        }
+        if (negative) {
+          tau1 = tau1 * R(0.5);
+          step++;
+          reject_run++;
+          cnt[3] += 1;
+          continue;
+        }
+        const double half = (double)tau * 0.5;
+#pragma unroll
+        for (int j = 0; j < MM; ++j) {
+          const R gn = g_int(md, j, xn);
+          r[j] += K[j];
+          G[j] = G[j] + half * ((double)g[j] + (double)gn);
+        }
+#pragma unroll
+        for (int s = 0; s < NM; ++s) x[s] = xn[s];
+        t = at_horizon ? T : t + (double)tau;
+        cnt[implicit_step ? 1 : 0] += 1;
+        step++;
+        reject_run = 0;
+        break;
+      }
+      }
+      if (burst > 0) {
+        ssa_burst(burst, a0);
+        step++;
+        reject_run = 0;
+      }
+    }
+
+    // write-back
+#pragma unroll
+    for (int s = 0; s < NM; ++s)
+      if (s < A.N) A.X[i * A.N + s] = x[s];
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      if (j < A.M) {
+        A.r[i * A.M + j] = r[j];
+        A.G[i * A.M + j] = G[j];
+      }
+    }
+    A.status[i] = status;
+    if (A.counters) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) A.counters[i * 4 + c] = cnt[c];
+    }
+  }
+};
+
+// Kernel: stage the model tables once per CTA, then simulate.  Plain form (queue null):
+// thread i runs trajectory i.  Persistent form: each thread claims trajectory indices
+// from the device queue until none is left, so a thread that finishes early
+// immediately refills its slot.
+template <int NM, int MM, class P>
+__global__ void __launch_bounds__(256) k_thread(const ThreadModel<NM, MM>* __restrict__ gmd,
+                                                const SimArgs args) {
+  __shared__ ThreadModel<NM, MM> smd;
+  __shared__ uint64_t mbar;
+  const bool staged = stage_model_bulk(&smd, gmd, (uint32_t)thread_model_bytes<NM, MM>(), &mbar);
+  long long i = args.queue ? (long long)atomicAdd(args.queue, 1ULL)
+                           : (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  while (i < args.n_traj) {
+    ThreadTraj<NM, MM, P>::run(smd, args, i);
+    if (!staged) args.status[i] |= ML_ST_STAGE_TIMEOUT;
+    if (!args.queue) break;
+    i = (long long)atomicAdd(args.queue, 1ULL);
+  }
+}
+
+}  // namespace mlk

@@ -1,0 +1,230 @@
+"""Thin Python binding of the C ABI in include/matleap.h (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps.  Device buffers are
+torch CUDA tensors (their data pointers are passed through), streams are torch streams;
+all simulation work runs in the CUDA library.  If the library has not been built, every
+call raises MatleapError: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmatleap.so")
+
+ML_OK, ML_ERR_ARG, ML_ERR_OOM, ML_ERR_CUDA, ML_ERR_TIMEOUT, ML_ERR_BUSY, ML_ERR_UNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6
+ML_ST_STEP_LIMIT, ML_ST_NEWTON_FAIL, ML_ST_REJECT_LIMIT, ML_ST_PTRS_CAP = 1, 2, 4, 8
+ML_ST_BAD_INPUT, ML_ST_STAGE_TIMEOUT = 16, 32
+ML_MODE_ADAPTIVE, ML_MODE_EXPLICIT_ONLY, ML_MODE_SSA_ONLY = 0, 1, 2
+ML_PREC_REF_FP64, ML_PREC_FAST_FP32 = 0, 1
+ML_FORM_PLAIN, ML_FORM_PERSISTENT = 0, 1
+ML_SHAPE_AUTO, ML_SHAPE_THREAD, ML_SHAPE_WARP = 0, 1, 2
+
+
+class MatleapError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class ml_sim_params(C.Structure):
+    _fields_ = [("eps", C.c_double), ("n_c", C.c_int32), ("ssa_factor", C.c_double),
+                ("n_ssa_explicit", C.c_int32), ("n_ssa_implicit", C.c_int32),
+                ("pe_delta", C.c_double), ("stiff_ratio", C.c_double),
+                ("newton_tol", C.c_double), ("newton_maxit", C.c_int32),
+                ("fd_h", C.c_double), ("max_steps", C.c_int64), ("max_reject", C.c_int32),
+                ("mode", C.c_int32), ("precision", C.c_int32), ("form", C.c_int32),
+                ("shape", C.c_int32), ("block_size", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("use_graph", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libmatleap.so (built in-tree by paper_1608_07058_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MatleapError(ML_ERR_UNSUPPORTED,
+                               f"CUDA library {LIB_PATH} is missing: run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        P, v = C.POINTER, C.c_void_p
+        L.ml_default_params.argtypes = [P(ml_sim_params)]
+        L.ml_last_error.restype = C.c_char_p
+        L.ml_model_create.argtypes = [C.c_int32, C.c_int32, P(C.c_int32), P(C.c_int32),
+                                      P(C.c_double), P(v)]
+        L.ml_model_destroy.argtypes = [v]
+        L.ml_model_num_pairs.argtypes = [v]
+        L.ml_model_last_launch_count.argtypes = [v]
+        L.ml_model_last_launch_count.restype = C.c_int64
+        sim = [v, C.c_int64, v, v, C.c_int32, v, C.c_int32, P(ml_sim_params), C.c_uint64,
+               C.c_uint64, v, v, v, v, v, v]
+        L.ml_simulate.argtypes = sim
+        L.ml_simulate_host.argtypes = sim
+        L.ml_autotune.argtypes = [v, C.c_int64, v, v, C.c_int32, v, C.c_int32,
+                                  P(ml_sim_params), C.c_uint64, C.c_int64, P(ml_sim_params), v]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != ML_OK:
+        raise MatleapError(rc, lib().ml_last_error().decode())
+
+
+def ml_last_error() -> str:
+    return lib().ml_last_error().decode()
+
+
+def ml_default_params(**overrides) -> ml_sim_params:
+    p = ml_sim_params()
+    _check(lib().ml_default_params(C.byref(p)))
+    for k, val in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, val)
+    return p
+
+
+class Model:
+    """Owns an ml_model handle."""
+
+    def __init__(self, handle: int, n_species: int, n_reactions: int):
+        self.handle = handle
+        self.N = n_species
+        self.M = n_reactions
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if self.handle:
+            lib().ml_model_destroy(C.c_void_p(self.handle))
+            self.handle = None
+
+
+def ml_model_create(orders, stoich, rates) -> Model:
+    """orders, stoich: (M, N) integer arrays; rates: (M,) float array (host)."""
+    o = np.ascontiguousarray(orders, np.int32)
+    s = np.ascontiguousarray(stoich, np.int32)
+    r = np.ascontiguousarray(rates, np.float64)
+    M, N = o.shape
+    h = C.c_void_p()
+    _check(lib().ml_model_create(N, M, o.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 s.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 r.ctypes.data_as(C.POINTER(C.c_double)), C.byref(h)))
+    return Model(h.value, N, M)
+
+
+def ml_model_destroy(model: Model):
+    model.close()
+
+
+def ml_model_num_pairs(model: Model) -> int:
+    rc = lib().ml_model_num_pairs(C.c_void_p(model.handle))
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+def ml_model_last_launch_count(model: Model) -> int:
+    return int(lib().ml_model_last_launch_count(C.c_void_p(model.handle)))
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None and not torch.cuda.is_available():
+        return C.c_void_p(None)  # the library reports the missing device itself
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def ml_simulate(model: Model, n_traj: int, x0, T, theta=None, params: Optional[ml_sim_params] = None,
+                seed: int = 0, traj_id_base: int = 0, out: Optional[dict] = None,
+                counters: bool = True, stream=None) -> dict:
+    """Launch a simulation on the current stream (asynchronous).  x0: int64 CUDA tensor
+    (N,) or (n_traj, N); T: float64 CUDA tensor (1,) or (n_traj,); theta: float64 CUDA
+    tensor (n_traj, M) or None.  Returns dict X, r, G, status[, counters] of CUDA tensors
+    (the given `out` buffers if passed)."""
+    import torch
+    dev = x0.device
+    if out is None:
+        out = {"X": torch.empty((n_traj, model.N), dtype=torch.int64, device=dev),
+               "r": torch.empty((n_traj, model.M), dtype=torch.int64, device=dev),
+               "G": torch.empty((n_traj, model.M), dtype=torch.float64, device=dev),
+               "status": torch.empty((n_traj,), dtype=torch.int32, device=dev)}
+        if counters:
+            out["counters"] = torch.empty((n_traj, 4), dtype=torch.int64, device=dev)
+    p = params if params is not None else ml_default_params()
+    _check(lib().ml_simulate(C.c_void_p(model.handle), n_traj, _ptr(theta), _ptr(x0),
+                             int(x0.dim() == 2), _ptr(T), int(T.numel() > 1), C.byref(p),
+                             seed, traj_id_base, _ptr(out["X"]), _ptr(out["r"]), _ptr(out["G"]),
+                             _ptr(out["status"]), _ptr(out.get("counters")),
+                             _stream_handle(stream)))
+    return out
+
+
+def ml_simulate_host(model: Model, n_traj: int, x0, T, theta=None,
+                     params: Optional[ml_sim_params] = None, seed: int = 0,
+                     traj_id_base: int = 0, out: Optional[dict] = None, counters: bool = True,
+                     stream=None) -> dict:
+    """Host-buffer variant: numpy (or pinned torch CPU) inputs and outputs; copies in,
+    simulates, copies out and synchronizes inside the call."""
+    def hp(a):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            return C.c_void_p(a.data_ptr())
+        return C.c_void_p(a.ctypes.data)
+    x0a = x0 if hasattr(x0, "data_ptr") else np.ascontiguousarray(x0, np.int64)
+    Ta = T if hasattr(T, "data_ptr") else np.ascontiguousarray(np.atleast_1d(T), np.float64)
+    tha = None if theta is None else (theta if hasattr(theta, "data_ptr")
+                                      else np.ascontiguousarray(theta, np.float64))
+    if out is None:
+        out = {"X": np.empty((n_traj, model.N), np.int64), "r": np.empty((n_traj, model.M), np.int64),
+               "G": np.empty((n_traj, model.M), np.float64), "status": np.empty(n_traj, np.uint32)}
+        if counters:
+            out["counters"] = np.empty((n_traj, 4), np.int64)
+    p = params if params is not None else ml_default_params()
+    ndim = x0a.dim() if hasattr(x0a, "dim") else x0a.ndim
+    nT = Ta.numel() if hasattr(Ta, "numel") else Ta.size
+    stream_h = _stream_handle(stream) if stream is not None else C.c_void_p(None)
+    _check(lib().ml_simulate_host(C.c_void_p(model.handle), n_traj, hp(tha), hp(x0a),
+                                  int(ndim == 2), hp(Ta), int(nT > 1), C.byref(p), seed,
+                                  traj_id_base, hp(out["X"]), hp(out["r"]), hp(out["G"]),
+                                  hp(out["status"]), hp(out.get("counters")), stream_h))
+    return out
+
+
+def ml_autotune(model: Model, n_traj: int, x0, T, theta=None,
+                params: Optional[ml_sim_params] = None, seed: int = 0, n_sample: int = 16384,
+                stream=None) -> ml_sim_params:
+    """Run the project autotuner on a sample of the given (device) inputs; returns the
+    chosen parameters (also remembered by the model for block_size = 0 calls)."""
+    p = params if params is not None else ml_default_params()
+    best = ml_sim_params()
+    _check(lib().ml_autotune(C.c_void_p(model.handle), n_traj, _ptr(theta), _ptr(x0),
+                             int(x0.dim() == 2), _ptr(T), int(T.numel() > 1), C.byref(p), seed,
+                             n_sample, C.byref(best), _stream_handle(stream)))
+    return best
+
+
+def model_from_crn(crn) -> Model:
+    """Convenience: an ml_model from a workloads.CRN."""
+    return ml_model_create(crn.orders, crn.stoich, crn.rates)

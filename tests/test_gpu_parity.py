@@ -1,0 +1,198 @@
+"""GPU path against the CPU oracle, through the C ABI.
+
+Reference precision: every trajectory bit-identical in X(T), r and status and G within
+1e-12 relative (here equal), with the same RNG keys, across the paper's workload shapes,
+small counts (critical reactions, rejections), every mode, the padded generic variant,
+and a full-size launch sampled by trajectory id.  Fast precision: ensemble statistics
+within 4 standard errors and KS p > 0.01 (Holm-corrected) against the oracle."""
+import numpy as np
+import pytest
+
+from paper_1608_07058_gb300 import workloads as W
+from tests import stats_util
+
+pytestmark = pytest.mark.gpu
+
+MAX_STEPS = 200_000
+G_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def ml():
+    import torch
+    from paper_1608_07058_gb300 import build, matleap
+    assert torch.cuda.is_available()
+    build.build()
+    matleap.lib()
+    return matleap
+
+
+def run_gpu(ml, crn, n, x0, T, theta=None, seed=0, base=0, model=None, **pkw):
+    import torch
+    d = torch.device("cuda")
+    model = model or ml.model_from_crn(crn)
+    x0t = torch.as_tensor(np.asarray(x0, np.int64), device=d)
+    Tt = torch.as_tensor(np.atleast_1d(np.asarray(T, np.float64)), device=d)
+    tht = None if theta is None else torch.as_tensor(np.asarray(theta, np.float64), device=d)
+    pkw.setdefault("max_steps", MAX_STEPS)
+    out = ml.ml_simulate(model, n, x0t, Tt, tht, params=ml.ml_default_params(**pkw), seed=seed,
+                         traj_id_base=base)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res["status"] = res["status"].astype(np.uint32)
+    return res
+
+
+def run_oracle(oracle, crn, n, x0, T, theta=None, seed=0, base=0, **pkw):
+    pkw.setdefault("max_steps", MAX_STEPS)
+    okw = {k: v for k, v in pkw.items() if k in oracle.Params.__dataclass_fields__}
+    return oracle.simulate(crn, n, x0, T, theta, params=oracle.Params(**okw), seed=seed,
+                           traj_id_base=base)
+
+
+def assert_bit_parity(g, o, label=""):
+    bad = np.flatnonzero((g["X"] != o["X"]).any(1) | (g["r"] != o["r"]).any(1))
+    assert bad.size == 0, f"{label}: {bad.size} trajectories differ, first {bad[:5]}"
+    assert np.array_equal(g["status"], o["status"]), label
+    assert np.array_equal(g["counters"], o["counters"]), label
+    den = np.maximum(np.abs(o["G"]), 1e-300)
+    rel = np.max(np.abs(g["G"] - o["G"]) / den) if o["G"].size else 0.0
+    assert rel <= G_RTOL, f"{label}: G rel err {rel}"
+
+
+def _generic_network():
+    # 5 species, 9 reactions, orders up to 3, a reversible pair: runs on the padded
+    # (8 species, 16 reactions) variant
+    return W._crn("generic5", 5, [
+        ({0: 1}, {1: 1}, 2.0), ({1: 1}, {0: 1}, 1.5),          # A <-> B
+        ({1: 2}, {2: 1}, 0.01), ({2: 1, 0: 1}, {3: 1}, 0.002),  # 2B -> C, A + C -> D
+        ({0: 3}, {4: 1}, 1e-5), ({0: 2, 1: 1}, {4: 2}, 1e-5),  # 3A -> E, 2A + B -> 2E
+        ({4: 1}, {}, 0.3), ({}, {0: 1}, 50.0), ({3: 1}, {0: 1, 2: 1}, 0.5),
+    ])
+
+
+CASES = {
+    "immigration_death": lambda: (W.config(0, n_traj=3000), {}),
+    "dimerisation": lambda: (W.config(1, n_traj=4000), {}),
+    "gene_expression": lambda: (W.config(2, n_traj=400), {}),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_ref_bit_parity_configs(ml, oracle, name):
+    w, kw = CASES[name]()
+    g = run_gpu(ml, w.crn, w.n_traj, w.x0, w.T, w.theta, seed=3, **kw)
+    o = run_oracle(oracle, w.crn, w.n_traj, w.x0, w.T, w.theta, seed=3, **kw)
+    assert_bit_parity(g, o, name)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("x0", [(12, 5, 0), (60, 20, 0)])
+def test_ref_bit_parity_small_counts_modes(ml, oracle, mode, x0):
+    crn = W.dimerisation()
+    g = run_gpu(ml, crn, 1500, list(x0), [1.5], seed=11, mode=mode)
+    o = run_oracle(oracle, crn, 1500, list(x0), [1.5], seed=11, mode=mode)
+    assert_bit_parity(g, o, f"mode{mode}")
+    assert (g["counters"][:, 3] > 0).any() or mode == 2 or x0[0] > 20
+
+
+def test_ref_bit_parity_generic_variant(ml, oracle):
+    crn = _generic_network()
+    x0 = [200, 100, 5, 0, 3]
+    g = run_gpu(ml, crn, 1500, x0, [2.0], seed=5)
+    o = run_oracle(oracle, crn, 1500, x0, [2.0], seed=5)
+    assert_bit_parity(g, o, "generic5")
+    assert g["counters"].sum(0)[0] > 0 and g["counters"].sum(0)[2] > 0
+
+
+def test_ref_bit_parity_per_traj_inputs_and_offsets(ml, oracle):
+    w = W.config(1, n_traj=700)
+    rng = np.random.default_rng(2)
+    x0 = rng.integers(0, 500, size=(700, 3))
+    T = rng.uniform(0.0, 0.3, size=700)
+    T[:5] = 0.0
+    theta = np.abs(w.crn.rates * rng.gamma(2.0, 0.5, size=(700, 4)))
+    g = run_gpu(ml, w.crn, 700, x0, T, theta, seed=2**40 + 9, base=123456)
+    o = run_oracle(oracle, w.crn, 700, x0, T, theta, seed=2**40 + 9, base=123456)
+    assert_bit_parity(g, o, "per-traj")
+
+
+def test_ref_full_size_sampled(ml, oracle):
+    """The full 100,000-trajectory dimerisation launch, sampled by trajectory id."""
+    w = W.config(1)
+    g = run_gpu(ml, w.crn, w.n_traj, w.x0, w.T, seed=1)
+    ids = np.unique(np.concatenate([np.arange(0, w.n_traj, 197), [w.n_traj - 1]]))
+    for i in ids:
+        o = run_oracle(oracle, w.crn, 1, w.x0, w.T, seed=1, base=int(i))
+        sub = {k: v[i:i + 1] for k, v in g.items()}
+        assert_bit_parity(sub, o, f"id {i}")
+    assert (g["status"] == 0).all()
+
+
+def test_persistent_graph_and_host_paths_identical(ml):
+    import torch
+    w = W.config(2, n_traj=3000)
+    model = ml.model_from_crn(w.crn)
+    base = run_gpu(ml, w.crn, w.n_traj, w.x0, w.T, w.theta, seed=4, model=model)
+    pers = run_gpu(ml, w.crn, w.n_traj, w.x0, w.T, w.theta, seed=4, model=model,
+                   form=ml.ML_FORM_PERSISTENT, block_size=64, ctas_per_sm=2)
+    graph1 = run_gpu(ml, w.crn, w.n_traj, w.x0, w.T, w.theta, seed=4, model=model,
+                     form=ml.ML_FORM_PERSISTENT, use_graph=1)
+    graph2 = run_gpu(ml, w.crn, w.n_traj, w.x0, w.T, w.theta, seed=4, model=model,
+                     form=ml.ML_FORM_PERSISTENT, use_graph=1)
+    host = ml.ml_simulate_host(model, w.n_traj, w.x0, w.T, w.theta,
+                               params=ml.ml_default_params(max_steps=MAX_STEPS), seed=4)
+    host["status"] = host["status"].astype(np.uint32)
+    for name, other in (("persistent", pers), ("graph1", graph1), ("graph2", graph2), ("host", host)):
+        for k in ("X", "r", "G", "status", "counters"):
+            assert np.array_equal(base[k], other[k]), (name, k)
+
+
+def test_zero_and_tiny_batches(ml, oracle):
+    import torch
+    crn = W.immigration_death()
+    m = ml.model_from_crn(crn)
+    x0 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    T = torch.full((1,), 5.0, dtype=torch.float64, device="cuda")
+    out = ml.ml_simulate(m, 0, x0, T)
+    assert out["X"].shape == (0, 1)
+    for n in (1, 31, 33, 257):
+        g = run_gpu(ml, crn, n, [0], [5.0], seed=8, model=m)
+        o = run_oracle(oracle, crn, n, [0], [5.0], seed=8)
+        assert_bit_parity(g, o, f"n={n}")
+
+
+def test_fast_statistics_dimerisation(ml, oracle):
+    w = W.config(1, n_traj=20000)
+    g = run_gpu(ml, w.crn, w.n_traj, w.x0, w.T, seed=21, precision=ml.ML_PREC_FAST_FP32,
+                form=ml.ML_FORM_PERSISTENT, use_graph=1)
+    o = run_oracle(oracle, w.crn, w.n_traj, w.x0, w.T, seed=21)
+    rows = stats_util.compare(g, o)
+    s = stats_util.summary(rows)
+    assert s["holm_pass_0.01"], (s, sorted(rows, key=lambda r: r[2])[:5])
+    assert (g["status"] == 0).all()
+
+
+def test_fast_statistics_immigration_death_and_gene(ml, oracle):
+    for cfg, n in ((0, 10000), (2, 3000)):
+        w = W.config(cfg, n_traj=n)
+        g = run_gpu(ml, w.crn, n, w.x0, w.T, w.theta, seed=31, precision=ml.ML_PREC_FAST_FP32)
+        o = run_oracle(oracle, w.crn, n, w.x0, w.T, w.theta, seed=31)
+        rows = stats_util.compare(g, o)
+        s = stats_util.summary(rows)
+        assert s["holm_pass_0.01"], (cfg, s, sorted(rows, key=lambda r: r[2])[:5])
+
+
+def test_autotune_picks_a_valid_shape(ml):
+    import torch
+    w = W.config(1, n_traj=20000)
+    model = ml.model_from_crn(w.crn)
+    d = torch.device("cuda")
+    x0 = torch.as_tensor(w.x0, device=d)
+    T = torch.as_tensor(w.T, device=d)
+    best = ml.ml_autotune(model, w.n_traj, x0, T, None,
+                          params=ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32,
+                                                      form=ml.ML_FORM_PERSISTENT),
+                          n_sample=8192)
+    assert best.shape in (ml.ML_SHAPE_THREAD, ml.ML_SHAPE_WARP)
+    assert best.block_size in (64, 128, 256)
