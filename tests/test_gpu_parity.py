@@ -93,16 +93,26 @@ def test_ref_bit_parity_small_counts_modes(ml, oracle, mode, x0):
     g = run_gpu(ml, crn, 1500, list(x0), [1.5], seed=11, mode=mode)
     o = run_oracle(oracle, crn, 1500, list(x0), [1.5], seed=11, mode=mode)
     assert_bit_parity(g, o, f"mode{mode}")
-    assert (g["counters"][:, 3] > 0).any() or mode == 2 or x0[0] > 20
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_ref_bit_parity_rejections(ml, oracle, mode):
+    # without critical reactions (n_c = 0) small counts make leaps overshoot: the
+    # negativity check rejects and halves tau
+    crn = W.dimerisation()
+    g = run_gpu(ml, crn, 2000, [12, 5, 0], [1.5], seed=13, mode=mode, n_c=0)
+    o = run_oracle(oracle, crn, 2000, [12, 5, 0], [1.5], seed=13, mode=mode, n_c=0)
+    assert_bit_parity(g, o, f"reject mode{mode}")
+    assert g["counters"][:, 3].sum() > 0
 
 
 def test_ref_bit_parity_generic_variant(ml, oracle):
     crn = _generic_network()
-    x0 = [200, 100, 5, 0, 3]
-    g = run_gpu(ml, crn, 1500, x0, [2.0], seed=5)
-    o = run_oracle(oracle, crn, 1500, x0, [2.0], seed=5)
-    assert_bit_parity(g, o, "generic5")
-    assert g["counters"].sum(0)[0] > 0 and g["counters"].sum(0)[2] > 0
+    for x0, T in (([200, 100, 5, 0, 3], 2.0), ([20000, 10000, 500, 0, 300], 0.5)):
+        g = run_gpu(ml, crn, 1500, x0, [T], seed=5)
+        o = run_oracle(oracle, crn, 1500, x0, [T], seed=5)
+        assert_bit_parity(g, o, f"generic5 {x0}")
+        assert g["counters"].sum(0)[:3].sum() > 0
 
 
 def test_ref_bit_parity_per_traj_inputs_and_offsets(ml, oracle):
