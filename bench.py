@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=15.0,
                     help="target CPU seconds for the oracle baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--jacobian", choices=["fd", "analytic"], default="analytic",
+                    help="Jacobian of the implicit solve, same for both forms")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--ncu", action="store_true",
                     help="skip the CPU leg, autotune, e2e and clocks (for profiler runs)")
@@ -142,11 +144,11 @@ def ops_from_counts(model_ops, counts):
 # ---------------------------------------------------------------------------------
 # reference arm and CPU baseline: the oracle on the host
 # ---------------------------------------------------------------------------------
-def oracle_rate(w, budget_s, seed=0, first_id=0):
+def oracle_rate(w, budget_s, seed=0, first_id=0, jacobian=1):
     """Time the oracle on a prefix sample of the workload sized to ~budget_s.
     Returns (trajectories/s, n_sample, seconds, outputs)."""
     from oracle import oracle as O
-    params = O.Params(max_steps=MAX_STEPS)
+    params = O.Params(max_steps=MAX_STEPS, jacobian=jacobian)
     n = min(w.n_traj, 200)
     t0 = time.perf_counter()
     O.simulate(w.crn, n, w.x0[:n] if w.x0.ndim == 2 else w.x0, w.T[:n] if w.T.size > 1 else w.T,
@@ -171,7 +173,8 @@ def run_reference(args):
     per_step_budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     rates, n_used = [], 0
     for s in range(args.warmup + args.steps):
-        rate, n, dt, _ = oracle_rate(w, per_step_budget, seed=s)
+        rate, n, dt, _ = oracle_rate(w, per_step_budget, seed=s,
+                                     jacobian=1 if args.jacobian == "analytic" else 0)
         if s >= args.warmup:
             rates.append(rate)
             n_used = n
@@ -234,13 +237,14 @@ def run_ours(args):
     theta = None if w.theta is None else torch.as_tensor(w.theta, device=dev)
     stream = torch.cuda.current_stream()
 
+    jac = ml.ML_JAC_ANALYTIC if args.jacobian == "analytic" else ml.ML_JAC_FD
     fast = ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32, form=ml.ML_FORM_PERSISTENT,
-                                use_graph=1, max_steps=MAX_STEPS)
+                                use_graph=1, max_steps=MAX_STEPS, jacobian=jac)
     if not args.ncu:
         best = ml.ml_autotune(model, B, x0, T, theta, params=fast, n_sample=min(B, 32768))
         fast.shape, fast.block_size, fast.ctas_per_sm = best.shape, best.block_size, best.ctas_per_sm
     plain = ml.ml_default_params(precision=ml.ML_PREC_REF_FP64, form=ml.ML_FORM_PLAIN,
-                                 max_steps=MAX_STEPS, block_size=128)
+                                 max_steps=MAX_STEPS, block_size=128, jacobian=jac)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
 
     def timed(params, seed0):
@@ -294,6 +298,7 @@ def run_ours(args):
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": workload_name(w), "form": "persistent refill kernel, CUDA graph, autotuned",
                        "precision": "FP32 propensities/tau/Poisson, FP64 t/G/Newton",
+                       "jacobian": args.jacobian,
                        "shape": {"shape": "thread" if fast.shape == ml.ML_SHAPE_THREAD else ("warp" if fast.shape == ml.ML_SHAPE_WARP else "auto"),
                                  "block_size": fast.block_size, "ctas_per_sm": fast.ctas_per_sm},
                        "l2": "flushed between steps (256 MB write)"},
@@ -355,14 +360,15 @@ def run_ours(args):
 
     # CPU oracle baseline and oracle-matched statistics (rank 0, N = 1 only for the baseline)
     if rank == 0 and not args.no_cpu and not args.ncu:
-        rate, n, dt, oout = oracle_rate(w, args.cpu_budget_s, seed=res_fast["last_seed"], first_id=id_base)
+        rate, n, dt, oout = oracle_rate(w, args.cpu_budget_s, seed=res_fast["last_seed"],
+                                        first_id=id_base, jacobian=jac)
         if world == 1:
             line["cpu_baseline"] = {"value": rate, "unit": "trajectories/s", "cores": 1, "kind": "oracle",
                                     "sample": f"first {n} trajectory ids of the workload ({dt:.1f} s), "
                                               f"single-threaded C oracle, FP64 reference algorithm"}
         from tests import stats_util
         g = {k: v[:n].cpu().numpy() for k, v in res_fast["last_out"].items()}
-        rows = stats_util.compare(g, oout)
+        rows = stats_util.compare(g, oout, g_res=stats_util.G_RESOLUTION_FAST)
         line["parity"] = {"fast_vs_oracle": stats_util.summary(rows), "n_compared": n,
                           "bad_status": res_fast["bad_status"]}
     if rank == 0:

@@ -80,13 +80,19 @@ extern "C" {
 #define ML_SHAPE_THREAD 1 /* one trajectory per thread (N <= 8, M <= 16)               */
 #define ML_SHAPE_WARP 2   /* one trajectory per warp (N <= 64, M <= 128)               */
 
+/* ---- Jacobian of the implicit solve (Section 1: estimated numerically, or the
+ *      symbolic Jacobian of Section 3) ------------------------------------------------- */
+#define ML_JAC_FD 0       /* forward differences                                          */
+#define ML_JAC_ANALYTIC 1 /* exact derivative of the mass-action polynomials              */
+
 typedef struct ml_model ml_model;
 
 /* Control parameters.  Defaults from ml_default_params():
  * eps 0.03, n_c 10, ssa_factor 10, n_ssa_explicit 100, n_ssa_implicit 10,
  * pe_delta 0.05, stiff_ratio 100, newton_tol 1e-10, newton_maxit 20, fd_h 1e-7,
  * max_steps 1e8, max_reject 64, mode ADAPTIVE, precision REF_FP64, form PLAIN,
- * shape AUTO, block_size 0 (tuned or default), ctas_per_sm 0, use_graph 0. */
+ * shape AUTO, block_size 0 (tuned or default), ctas_per_sm 0, use_graph 0,
+ * jacobian FD. */
 typedef struct {
   double eps;             /* Cao 2006 bound on the relative change of each reactant    */
   int32_t n_c;            /* critical threshold (Section 2)                            */
@@ -107,6 +113,7 @@ typedef struct {
   int32_t block_size;     /* threads per CTA; 0 = autotuned value or default           */
   int32_t ctas_per_sm;    /* persistent form: resident CTAs per SM; 0 = tuned/default  */
   int32_t use_graph;      /* persistent form: launch through a cached CUDA graph       */
+  int32_t jacobian;       /* ML_JAC_*: Jacobian of the propensities in implicit leaps  */
 } ml_sim_params;
 
 /* Fills *p with the defaults above.  Returns ML_ERR_ARG if p is NULL. */

@@ -359,6 +359,13 @@ static double g_int(const model_t* md, int32_t j, const int64_t* x) {
   return v;
 }
 
+/* d/dv C(v, m) for m = 1, 2, 3: 1, v - 1/2, (3 v^2 - 6 v + 2) / 6, in this order. */
+static double comb_factor_deriv(double v, int32_t m) {
+  if (m == 1) return 1.0;
+  if (m == 2) return v - 0.5;
+  return ((3.0 * (v * v) - 6.0 * v) + 2.0) / 6.0;
+}
+
 /* g_j at a real state (implicit solve): the same polynomial without the clamp. */
 static double g_real(const model_t* md, int32_t j, const double* y) {
   double v = 1.0;
@@ -366,6 +373,19 @@ static double g_real(const model_t* md, int32_t j, const double* y) {
     int32_t m = md->ord[j * md->N + s];
     if (m == 0) continue;
     v = v * comb_factor(y[s], m);
+  }
+  return v;
+}
+
+/* Exact partial derivative of g_j with respect to y_q: the product in increasing s with
+ * the factor of species q replaced by its derivative (0 if q is not a reactant). */
+static double g_real_deriv(const model_t* md, int32_t j, const double* y, int32_t q) {
+  if (md->ord[j * md->N + q] == 0) return 0.0;
+  double v = 1.0;
+  for (int32_t s = 0; s < md->N; ++s) {
+    int32_t m = md->ord[j * md->N + s];
+    if (m == 0) continue;
+    v = v * (s == q ? comb_factor_deriv(y[s], m) : comb_factor(y[s], m));
   }
   return v;
 }
@@ -436,7 +456,8 @@ double mlo_tau_select(int32_t N, int32_t M, const int32_t* orders, const int32_t
  * means a_j(x) tau for the non-critical reactions, solve for the real state y
  *   y = c + tau sum_j nu_j a_j(y),   c = x + sum_j nu_j (P_j - a_j(x) tau)
  * by Newton's method with a forward-difference Jacobian of the propensities (the
- * paper's "estimated numerically", Section 1):
+ * paper's "estimated numerically", Section 1) or, on request, the exact derivative of
+ * the mass-action polynomials (the paper's symbolic Jacobian, Section 3):
  *   F(y) = (y - c) - tau sum_j nu_j a_j(y),
  *   J[s][q] = [s == q] - tau sum_j nu_js D_jq,  D_jq = (a_j(y + h e_q) - a_j(y)) / h,
  *   h = ((y_q + fd_h max(1,|y_q|)) - y_q);
@@ -480,8 +501,15 @@ static int implicit_solve_md(const model_t* md, const double* th, const int64_t*
       }
       F[s] = (y[s] - c[s]) - tau * acc;
     }
-    /* forward differences, one species at a time */
-    for (int32_t q = 0; q < N; ++q) {
+    /* D_jq = d a_j / d y_q: exact, or forward differences one species at a time */
+    if (p->jacobian == MLO_JAC_ANALYTIC) {
+      for (int32_t q = 0; q < N; ++q)
+        for (int32_t j = 0; j < M; ++j)
+          D[j * N + q] = (nc[j] && md->ord[j * N + q] != 0)
+                             ? th[j] * g_real_deriv(md, j, y, q)
+                             : 0.0;
+    }
+    for (int32_t q = 0; q < N && p->jacobian != MLO_JAC_ANALYTIC; ++q) {
       double aq = fabs(y[q]);
       double h = p->fd_h * (aq > 1.0 ? aq : 1.0);
       for (int32_t s = 0; s < N; ++s) yq[s] = y[s];
@@ -592,6 +620,7 @@ void mlo_default_params(mlo_params* p) {
   p->max_steps = 100000000;
   p->max_reject = 64;
   p->mode = MLO_MODE_ADAPTIVE;
+  p->jacobian = MLO_JAC_FD;
 }
 
 /* ------------------------------------------------------------------------------------

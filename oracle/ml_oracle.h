@@ -49,7 +49,14 @@ typedef struct {
   int64_t max_steps;      /* safety cap on outer steps per trajectory                 */
   int32_t max_reject;     /* consecutive rejections before forcing an SSA burst       */
   int32_t mode;           /* MLO_MODE_*                                               */
+  int32_t jacobian;       /* MLO_JAC_FD or MLO_JAC_ANALYTIC                           */
 } mlo_params;
+
+/* Jacobian of the propensities in the implicit solve: forward differences (the paper's
+ * "estimated numerically") or the exact derivative of the mass-action polynomials (the
+ * paper's symbolic Jacobian, Section 3). */
+#define MLO_JAC_FD 0
+#define MLO_JAC_ANALYTIC 1
 
 void mlo_default_params(mlo_params* p);
 

@@ -22,7 +22,7 @@ class _Params(C.Structure):
                 ("pe_delta", C.c_double), ("stiff_ratio", C.c_double),
                 ("newton_tol", C.c_double), ("newton_maxit", C.c_int32),
                 ("fd_h", C.c_double), ("max_steps", C.c_int64),
-                ("max_reject", C.c_int32), ("mode", C.c_int32)]
+                ("max_reject", C.c_int32), ("mode", C.c_int32), ("jacobian", C.c_int32)]
 
 
 @dataclass
@@ -40,6 +40,7 @@ class Params:
     max_steps: int = 100_000_000
     max_reject: int = 64
     mode: int = MODE_ADAPTIVE
+    jacobian: int = 0  # 0 forward differences, 1 exact (analytic)
 
     def c(self) -> _Params:
         return _Params(**asdict(self))

@@ -191,8 +191,9 @@ int thread_variant_for(const ml_model& m) {
 }
 
 bool warp_fits(const ml_model& m) {
-  return m.N <= mlk::kWarpMaxN && m.M <= mlk::kWarpMaxM &&
-         (size_t)(m.M * m.N) <= (size_t)mlk::kWarpMaxM * 8;
+  size_t nnz = 0;
+  for (int32_t v : m.nu) nnz += v != 0;
+  return m.N <= mlk::kWarpMaxN && m.M <= mlk::kWarpMaxM && nnz <= (size_t)mlk::kWarpMaxM * 8;
 }
 
 mlk::KernelEntry thread_entry(int precision, int variant) {
@@ -251,6 +252,8 @@ int check_params(const ml_sim_params& p) {
     return fail(ML_ERR_ARG, "block_size must be 0 or a multiple of 32 in [32, 256]");
   if (p.ctas_per_sm < 0 || p.ctas_per_sm > 32)
     return fail(ML_ERR_ARG, "ctas_per_sm must be in [0, 32]");
+  if (p.jacobian != ML_JAC_FD && p.jacobian != ML_JAC_ANALYTIC)
+    return fail(ML_ERR_ARG, "unknown jacobian %d", p.jacobian);
   return ML_OK;
 }
 
@@ -340,7 +343,7 @@ int make_plan(ml_model* m, DeviceState& st, const ml_sim_params& p, int64_t n_tr
                            : (tuned_here && tuned->block ? tuned->block
                                                          : (shape == ML_SHAPE_THREAD ? 128 : 128));
   const int per_cta = shape == ML_SHAPE_THREAD ? block : block / 32;  // trajectories
-  plan->smem = shape == ML_SHAPE_WARP ? mlk::warp_smem_bytes(block / 32) : 0;
+  plan->smem = shape == ML_SHAPE_WARP ? mlk::warp_smem_bytes(block / 32, m->N, m->M, p.precision) : 0;
   if (plan->smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(plan->entry.kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -403,6 +406,7 @@ void fill_args(const ml_model* m, const ml_sim_params& p, int64_t n_traj, const 
   a->newton_maxit = p.newton_maxit;
   a->max_reject = p.max_reject;
   a->mode = p.mode;
+  a->jacobian = p.jacobian;
   a->queue = nullptr;
 }
 
@@ -493,6 +497,7 @@ int ml_default_params(ml_sim_params* p) {
   p->block_size = 0;
   p->ctas_per_sm = 0;
   p->use_graph = 0;
+  p->jacobian = ML_JAC_FD;
   return ML_OK;
 }
 

@@ -1,12 +1,33 @@
-// One trajectory per warp (large networks).  Not built yet: the entries are empty and
-// the host API reports such models as unsupported.
-#include "ml_internal.h"
+// One-trajectory-per-warp kernel for one arithmetic:
+//   ML_FAST = 0: reference precision (compile with -fmad=false), 1: fast precision.
+#include "warp_core.cuh"
 
 namespace mlk {
 #if ML_FAST
-KernelEntry warp_entry_fast() { return KernelEntry{nullptr, nullptr}; }
+using WPrec = PrecFast;
 #else
-KernelEntry warp_entry_ref() { return KernelEntry{nullptr, nullptr}; }
-size_t warp_smem_bytes(int) { return 0; }
+using WPrec = PrecRef;
+#endif
+
+namespace {
+cudaError_t launch(const void* dm, const SimArgs& a, int grid, int block, size_t smem,
+                   cudaStream_t s) {
+  k_warp<WPrec><<<grid, block, smem, s>>>(static_cast<const WarpModel*>(dm), a);
+  return cudaGetLastError();
+}
+}  // namespace
+
+#if ML_FAST
+KernelEntry warp_entry_fast() {
+  return KernelEntry{&launch, reinterpret_cast<const void*>(&k_warp<WPrec>)};
+}
+#else
+KernelEntry warp_entry_ref() {
+  return KernelEntry{&launch, reinterpret_cast<const void*>(&k_warp<WPrec>)};
+}
+size_t warp_smem_bytes(int warps, int N, int M, int precision) {
+  const int rbytes = precision == ML_PREC_FAST_FP32 ? 4 : 8;
+  return (sizeof(WarpModel) + 15) / 16 * 16 + (size_t)warps * warp_slab_bytes(N, M, rbytes);
+}
 #endif
 }  // namespace mlk

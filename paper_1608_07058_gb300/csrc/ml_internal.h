@@ -101,6 +101,7 @@ struct SimArgs {
   int32_t newton_maxit;
   int32_t max_reject;
   int32_t mode;
+  int32_t jacobian;  // ML_JAC_*
   // persistent form: next unclaimed trajectory (zeroed before each launch)
   unsigned long long* queue;
 };
@@ -127,6 +128,7 @@ KernelEntry thread_entry_fast_3();
 KernelEntry warp_entry_ref();
 KernelEntry warp_entry_fast();
 // Dynamic shared memory of the warp kernel for a CTA of `warps` warps.
-size_t warp_smem_bytes(int warps);
+size_t warp_smem_bytes(int warps, int N, int M, int precision);
+
 
 }  // namespace mlk

@@ -47,6 +47,13 @@ __device__ __forceinline__ R comb_factor(R v, int m) {
   return ((v * (v - R(1))) * (v - R(2))) / R(6);
 }
 
+// d/dv C(v, m): 1, v - 1/2, (3 v^2 - 6 v + 2) / 6, in this operation order.
+__device__ __forceinline__ double comb_factor_deriv(double v, int m) {
+  if (m == 1) return 1.0;
+  if (m == 2) return v - 0.5;
+  return ((3.0 * (v * v) - 6.0 * v) + 2.0) / 6.0;
+}
+
 // Highest-order-reaction factor h_s (Cao 2006) from the species' flags and count.
 template <class R>
 __device__ __forceinline__ R hor_factor(uint8_t f, long long x) {
@@ -82,6 +89,7 @@ struct PrecRef {
     return refmath::log_factorial_ref(k);
   }
   __device__ static __forceinline__ R sqrt(R x) { return ::sqrt(x); }
+  __device__ static __forceinline__ R log1p(R x) { return ::log1p(x); }  // unused
   __device__ static __forceinline__ R inf() {
     return __longlong_as_double(0x7ff0000000000000LL);
   }
@@ -93,12 +101,15 @@ struct PrecFast {
   __device__ static __forceinline__ R u(const Words4& w, int k) {
     return k == 0 ? u01_f32(w.w0) : u01_f32(w.w2);
   }
-  __device__ static __forceinline__ R log(R x) { return __logf(x); }
+  // accurate logf: the waiting times -log(u)/a0 need relative accuracy for u near 1,
+  // where the hardware approximation's absolute error would bias the clock
+  __device__ static __forceinline__ R log(R x) { return logf(x); }
   __device__ static __forceinline__ R exp(R x) { return __expf(x); }
   __device__ static __forceinline__ R lfact(long long k) {
     return lgammaf((float)k + 1.0f);
   }
   __device__ static __forceinline__ R sqrt(R x) { return sqrtf(x); }
+  __device__ static __forceinline__ R log1p(R x) { return log1pf(x); }
   __device__ static __forceinline__ R inf() { return __int_as_float(0x7f800000); }
 };
 
@@ -114,6 +125,7 @@ struct PrecWide {
   __device__ static __forceinline__ R exp(R x) { return ::exp(x); }
   __device__ static __forceinline__ R lfact(long long k) { return ::lgamma((double)k + 1.0); }
   __device__ static __forceinline__ R sqrt(R x) { return ::sqrt(x); }
+  __device__ static __forceinline__ R log1p(R x) { return ::log1p(x); }
   __device__ static __forceinline__ R inf() {
     return __longlong_as_double(0x7ff0000000000000LL);
   }
@@ -143,7 +155,18 @@ __device__ __noinline__ long long poisson_ptrs(typename P::R mu, uint32_t k0, ui
     if (us >= R(0.07) && V <= v_r) return (long long)kd;
     if (kd < R(0) || (us < R(0.013) && V > us)) continue;
     const R lhs = (P::log(V) + P::log(inv_alpha)) - P::log(a / (us * us) + b);
-    const R rhs = (-mu + kd * loglam) - P::lfact((long long)kd);
+    R rhs;
+    if (P::kRef || kd < R(10)) {
+      rhs = (-mu + kd * loglam) - P::lfact((long long)kd);
+    } else {
+      // log of the Poisson pmf without cancellation: with z = k + 1 and Stirling's series
+      // for log Gamma(z), -mu + k log mu - log k! =
+      //   (z - mu) + (z - 1) log1p((mu - z)/z) - log(z)/2 - log(2 pi)/2 - 1/(12 z) + 1/(360 z^3)
+      const R z = kd + R(1);
+      const R iz = R(1) / z;
+      rhs = ((z - mu) + (z - R(1)) * P::log1p((mu - z) * iz)) - R(0.5) * P::log(z) -
+            R(0.91893853320467274178) - iz * (R(1) / R(12) - (iz * iz) * (R(1) / R(360)));
+    }
     if (lhs <= rhs) return (long long)kd;
   }
   status |= ML_ST_PTRS_CAP;
@@ -209,6 +232,18 @@ struct ThreadTraj {
     return v;
   }
 
+  // exact d g_j / d y_q: the product with species q's factor replaced by its derivative
+  __device__ static __forceinline__ double g_real_deriv(const Model& md, int j,
+                                                        const double (&y)[NM], int q) {
+    double v = 1.0;
+#pragma unroll
+    for (int s = 0; s < NM; ++s) {
+      const int m = md.ord[j][s];
+      if (m != 0) v = v * (s == q ? comb_factor_deriv(y[s], m) : comb_factor<double>(y[s], m));
+    }
+    return v;
+  }
+
   __device__ static __forceinline__ void eval_props(const Model& md, const long long (&x)[NM],
                                                     const R (&th)[MM], R (&g)[MM], R (&a)[MM]) {
 #pragma unroll
@@ -256,7 +291,7 @@ struct ThreadTraj {
                                        const long long (&x)[NM], uint32_t nc,
                                        const long long (&Pk)[MM], const R (&a)[MM],
                                        double tau, double tol, int maxit, double fd_h,
-                                       double (&y)[NM]) {
+                                       bool analytic, double (&y)[NM]) {
     double c[NM];
 #pragma unroll
     for (int s = 0; s < NM; ++s) {
@@ -287,19 +322,27 @@ struct ThreadTraj {
       }
 #pragma unroll
       for (int q = 0; q < NM; ++q) {
-        const double aq = fabs(y[q]);
-        const double h = fd_h * (aq > 1.0 ? aq : 1.0);
-        double yq[NM];
-#pragma unroll
-        for (int s = 0; s < NM; ++s) yq[s] = y[s];
-        yq[q] = y[q] + h;
-        const double he = yq[q] - y[q];
         double Dq[MM];
+        if (analytic) {
 #pragma unroll
-        for (int j = 0; j < MM; ++j)
-          Dq[j] = (((nc >> j) & 1u) && md.ord[j][q] != 0)
-                      ? ((double)th[j] * g_real(md, j, yq) - ay[j]) / he
-                      : 0.0;
+          for (int j = 0; j < MM; ++j)
+            Dq[j] = (((nc >> j) & 1u) && md.ord[j][q] != 0)
+                        ? (double)th[j] * g_real_deriv(md, j, y, q)
+                        : 0.0;
+        } else {
+          const double aq = fabs(y[q]);
+          const double h = fd_h * (aq > 1.0 ? aq : 1.0);
+          double yq[NM];
+#pragma unroll
+          for (int s = 0; s < NM; ++s) yq[s] = y[s];
+          yq[q] = y[q] + h;
+          const double he = yq[q] - y[q];
+#pragma unroll
+          for (int j = 0; j < MM; ++j)
+            Dq[j] = (((nc >> j) & 1u) && md.ord[j][q] != 0)
+                        ? ((double)th[j] * g_real(md, j, yq) - ay[j]) / he
+                        : 0.0;
+        }
 #pragma unroll
         for (int s = 0; s < NM; ++s) {
           double acc = 0.0;
@@ -366,6 +409,39 @@ struct ThreadTraj {
     return 1;
   }
 
+  // Inverse-CDF pick of a reaction with probability v_j / sum v, from the second uniform
+  // of block w (words 2, 3).  Reference: sequential prefix sums in index order (the
+  // canonical order), target u * sum with the lane-tree sum.  Fast: the same search over
+  // FP64 prefix sums of the FP32 values with a 52-bit uniform, so reactions far below the
+  // total (propensities spanning many decades) keep their exact share.  Rounding that
+  // leaves no hit picks the last positive entry.
+  __device__ static __forceinline__ int pick_reaction(const R (&v)[MM], const Words4& w) {
+    int pk = -1, last = -1;
+    if (P::kRef) {
+      const R target = P::u(w, 1) * lane_tree_sum<MM, R>(v);
+      R acc = R(0);
+#pragma unroll
+      for (int j = 0; j < MM; ++j) {
+        if (v[j] > R(0)) last = j;
+        acc = acc + v[j];
+        if (pk < 0 && target < acc) pk = j;
+      }
+    } else {
+      double tot = 0.0;
+#pragma unroll
+      for (int j = 0; j < MM; ++j) tot += (double)v[j];
+      const double target = u01_f64(w.w2, w.w3) * tot;
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < MM; ++j) {
+        if (v[j] > R(0)) last = j;
+        acc += (double)v[j];
+        if (pk < 0 && target < acc) pk = j;
+      }
+    }
+    return pk < 0 ? last : pk;
+  }
+
   // The whole trajectory.
   __device__ static void run(const Model& md, const SimArgs& A, long long i) {
     const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
@@ -426,7 +502,6 @@ struct ThreadTraj {
         }
         const Words4 w = philox_block(k0, k1, id, step, Mr + 2u, (uint32_t)b);
         const R u1 = P::u(w, 0);
-        const R u2 = P::u(w, 1);
         const R dt = -P::log(u1) / a0;
         const double tn = t + (double)dt;
         if (tn > T) {
@@ -437,18 +512,12 @@ struct ThreadTraj {
           return;
         }
 #pragma unroll
-        for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)g[j] * (double)dt;
-        t = tn;
-        const R target = u2 * a0;
-        R acc = R(0);
-        int pick = -1, last = -1;
-#pragma unroll
         for (int j = 0; j < MM; ++j) {
-          if (a[j] > R(0)) last = j;
-          acc = acc + a[j];
-          if (pick < 0 && target < acc) pick = j;
+          if (P::kRef) G[j] = G[j] + (double)g[j] * (double)dt;
+          else G[j] = G[j] + (double)(g[j] * dt);  // FP32 increment, FP64 accumulation
         }
-        if (pick < 0) pick = last;
+        t = tn;
+        const int pick = pick_reaction(a, w);
 #pragma unroll
         for (int s = 0; s < NM; ++s) x[s] += md.nu[pick][s];
 #pragma unroll
@@ -555,16 +624,7 @@ struct ThreadTraj {
         for (int j = 0; j < MM; ++j) K[j] = 0;
         if (crit_fire) {
           const Words4 w = philox_block(k0, k1, id, step, Mr + 1u, 0u);
-          const R target = P::u(w, 0) * a0c;
-          R acc = R(0);
-          int pick = -1, last = -1;
-#pragma unroll
-          for (int j = 0; j < MM; ++j) {
-            if (ac[j] > R(0)) last = j;
-            acc = acc + ac[j];
-            if (pick < 0 && target < acc) pick = j;
-          }
-          if (pick < 0) pick = last;
+          const int pick = pick_reaction(ac, Words4{0u, 0u, w.w0, w.w1});
 #pragma unroll
           for (int j = 0; j < MM; ++j) K[j] = (j == pick) ? 1 : 0;
         }
@@ -579,7 +639,7 @@ struct ThreadTraj {
           double y[NM];
           const double taud = (double)tau;
           const int rc = implicit_solve(md, th, x, nc, K, a, taud, A.newton_tol,
-                                        A.newton_maxit, A.fd_h, y);
+                                        A.newton_maxit, A.fd_h, A.jacobian == ML_JAC_ANALYTIC, y);
           if (rc != 0) {
             status |= ML_ST_NEWTON_FAIL;
             implicit = false;
@@ -615,11 +675,13 @@ struct ThreadTraj {
           continue;
         }
         const double half = (double)tau * 0.5;
+        const R half_r = tau * R(0.5);
 #pragma unroll
         for (int j = 0; j < MM; ++j) {
           const R gn = g_int(md, j, xn);
           r[j] += K[j];
-          G[j] = G[j] + half * ((double)g[j] + (double)gn);
+          if (P::kRef) G[j] = G[j] + half * ((double)g[j] + (double)gn);
+          else G[j] = G[j] + (double)(half_r * (g[j] + gn));  // FP32 increment
         }
 #pragma unroll
         for (int s = 0; s < NM; ++s) x[s] = xn[s];

@@ -150,11 +150,16 @@ struct WarpTraj {
     return tau;
   }
 
-  // Picks the reaction whose prefix interval of `v` contains `target` (v in shared
-  // memory, owned values in vl).  Reference: sequential prefix in index order, the last
-  // positive entry if rounding leaves none.  Fast: prefix over lane-major order.
-  __device__ static int pick(const R* v, const R (&vl)[kRPL], R target, int M, int lane) {
+  // Inverse-CDF pick of a reaction with probability v_j / sum v (v in shared memory,
+  // owned values in vl) from the second uniform of block w.  Reference: sequential prefix
+  // in index order with target u * (lane-tree sum), the canonical order.  Fast: FP64
+  // prefix sums of the FP32 values over lane-major order with a 52-bit uniform, so
+  // reactions many decades below the total keep their exact share.  Rounding that leaves
+  // no hit picks the last positive entry.  All lanes return the same index.
+  __device__ static int pick(const R* v, const R (&vl)[kRPL], const Words4& w, int M,
+                             int lane) {
     if (P::kRef) {
+      const R target = P::u(w, 1) * tree_sum(vl, lane, M);
       R acc = R(0);
       int pk = -1, last = -1;
       for (int j = 0; j < M; ++j) {
@@ -168,32 +173,33 @@ struct WarpTraj {
       }
       return pk < 0 ? last : pk;
     } else {
-      R S = R(0);
+      double S = 0.0;
 #pragma unroll
       for (int q = 0; q < kRPL; ++q)
-        if (lane + 32 * q < M) S = S + vl[q];
-      R E = S;  // inclusive scan over lanes
+        if (lane + 32 * q < M) S += (double)vl[q];
+      double E = S;  // inclusive scan over lanes
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
-        const R o = __shfl_up_sync(0xffffffffu, E, d);
-        if (lane >= d) E = E + o;
+        const double o = __shfl_up_sync(0xffffffffu, E, d);
+        if (lane >= d) E += o;
       }
-      const unsigned hit = __ballot_sync(0xffffffffu, target < E && S > R(0));
+      const double target = u01_f64(w.w2, w.w3) * __shfl_sync(0xffffffffu, E, 31);
+      const unsigned hit = __ballot_sync(0xffffffffu, target < E && S > 0.0);
       int src;
       if (hit) src = __ffs(hit) - 1;
       else {
-        const unsigned pos = __ballot_sync(0xffffffffu, S > R(0));
+        const unsigned pos = __ballot_sync(0xffffffffu, S > 0.0);
         src = pos ? 31 - __clz(pos) : 0;
       }
       int pk = -1, last = -1;
       if (lane == src) {
-        R acc = E - S;
+        double acc = E - S;
 #pragma unroll
         for (int q = 0; q < kRPL; ++q) {
           const int j = lane + 32 * q;
           if (j < M && vl[q] > R(0)) {
             last = j;
-            acc = acc + vl[q];
+            acc += (double)vl[q];
             if (pk < 0 && target < acc) pk = j;
           }
         }
@@ -207,7 +213,7 @@ struct WarpTraj {
   __device__ static int implicit_solve(const WarpModel& md, const WarpSlab& sl,
                                        const R (&th)[kRPL], const uint32_t (&nc)[kRPL],
                                        const R* a, double tau, double tol, int maxit,
-                                       double fd_h, int lane) {
+                                       double fd_h, bool analytic, int lane) {
     const int N = md.N, M = md.M;
     double c[kSPL];
 #pragma unroll
@@ -254,13 +260,23 @@ struct WarpTraj {
           for (int k = 0; k < 3; ++k) {
             double dv = 0.0;
             if (k < nr && bit(nc, j)) {
-              const int sq = md.rsp[j][k];
-              const double yq = sl.y[sq];
-              const double aq = fabs(yq);
-              const double h = fd_h * (aq > 1.0 ? aq : 1.0);
-              const double yp = yq + h;
-              const double he = yp - yq;
-              dv = ((double)th[q] * g_real(md, j, sl.y, sq, yp) - sl.ay[j]) / he;
+              if (analytic) {
+                double v = 1.0;
+                for (int kk = 0; kk < nr; ++kk) {
+                  const double ys = sl.y[md.rsp[j][kk]];
+                  const int m = md.rmul[j][kk];
+                  v = v * (kk == k ? comb_factor_deriv(ys, m) : comb_factor<double>(ys, m));
+                }
+                dv = (double)th[q] * v;
+              } else {
+                const int sq = md.rsp[j][k];
+                const double yq = sl.y[sq];
+                const double aq = fabs(yq);
+                const double h = fd_h * (aq > 1.0 ? aq : 1.0);
+                const double yp = yq + h;
+                const double he = yp - yq;
+                dv = ((double)th[q] * g_real(md, j, sl.y, sq, yp) - sl.ay[j]) / he;
+              }
             }
             sl.D[j * 3 + k] = dv;
           }
@@ -308,7 +324,7 @@ struct WarpTraj {
             piv = op;
           }
         }
-        if (best == 0.0) return 2;
+        if (!(best > 0.0) || piv >= N) return 2;  // zero or non-finite column: singular
         if (piv != k) {
           for (int cc = lane; cc < N; cc += 32) {
             const double t = sl.J[(size_t)k * N + cc];
@@ -445,7 +461,6 @@ struct WarpTraj {
         }
         const Words4 w = philox_block(k0, k1, id, step, Mr + 2u, (uint32_t)b);
         const R u1 = P::u(w, 0);
-        const R u2 = P::u(w, 1);
         const R dt = -P::log(u1) / a0;
         const double tn = t + (double)dt;
         if (tn > T) {
@@ -456,15 +471,20 @@ struct WarpTraj {
           return;
         }
 #pragma unroll
-        for (int q = 0; q < kRPL; ++q) G[q] = G[q] + (double)g[q] * (double)dt;
+        for (int q = 0; q < kRPL; ++q) {
+          if (P::kRef) G[q] = G[q] + (double)g[q] * (double)dt;
+          else G[q] = G[q] + (double)(g[q] * dt);  // FP32 increment, FP64 accumulation
+        }
         t = tn;
-        const int pk = pick(a_s, a, u2 * a0, M, lane);
-        const int e0 = md.rx_ptr[pk], e1 = md.rx_ptr[pk + 1];
-        if (lane < e1 - e0) sl.x[md.rx_s[e0 + lane]] += md.rx_nu[e0 + lane];
+        const int pk = pick(a_s, a, w, M, lane);
+        if (pk >= 0) {
+          const int e0 = md.rx_ptr[pk], e1 = md.rx_ptr[pk + 1];
+          for (int e = e0 + lane; e < e1; e += 32) sl.x[md.rx_s[e]] += md.rx_nu[e];
 #pragma unroll
-        for (int q = 0; q < kRPL; ++q)
-          if (lane + 32 * q == pk) r[q] += 1;
-        cnt[2] += 1;
+          for (int q = 0; q < kRPL; ++q)
+            if (lane + 32 * q == pk) r[q] += 1;
+          cnt[2] += 1;
+        }
         __syncwarp();
       }
     };
@@ -584,7 +604,7 @@ struct WarpTraj {
           int cpk = -1;
           if (crit_fire) {
             const Words4 w = philox_block(k0, k1, id, step, Mr + 1u, 0u);
-            cpk = pick(ac_s, ac, P::u(w, 0) * a0c, M, lane);
+            cpk = pick(ac_s, ac, Words4{0u, 0u, w.w0, w.w1}, M, lane);
           }
           const bool implicit_step = implicit && tau > tau_ex;
           long long K[kRPL];
@@ -602,7 +622,8 @@ struct WarpTraj {
           if (implicit_step) {
             const double taud = (double)tau;
             const int rc = implicit_solve(md, sl, th, nc, a_s, taud, A.newton_tol,
-                                          A.newton_maxit, A.fd_h, lane);
+                                          A.newton_maxit, A.fd_h,
+                                          A.jacobian == ML_JAC_ANALYTIC, lane);
             if (rc != 0) {
               status |= ML_ST_NEWTON_FAIL;
               implicit = false;
@@ -652,13 +673,15 @@ struct WarpTraj {
             continue;
           }
           const double half = (double)tau * 0.5;
+          const R half_r = tau * R(0.5);
 #pragma unroll
           for (int q = 0; q < kRPL; ++q) {
             const int j = lane + 32 * q;
             if (j < M) {
               const R gn = g_int(md, j, sl.xn);
               r[q] += K[q];
-              G[q] = G[q] + half * ((double)g[q] + (double)gn);
+              if (P::kRef) G[q] = G[q] + half * ((double)g[q] + (double)gn);
+              else G[q] = G[q] + (double)(half_r * (g[q] + gn));  // FP32 increment
             }
           }
           __syncwarp();

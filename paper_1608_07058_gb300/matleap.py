@@ -24,6 +24,7 @@ ML_MODE_ADAPTIVE, ML_MODE_EXPLICIT_ONLY, ML_MODE_SSA_ONLY = 0, 1, 2
 ML_PREC_REF_FP64, ML_PREC_FAST_FP32 = 0, 1
 ML_FORM_PLAIN, ML_FORM_PERSISTENT = 0, 1
 ML_SHAPE_AUTO, ML_SHAPE_THREAD, ML_SHAPE_WARP = 0, 1, 2
+ML_JAC_FD, ML_JAC_ANALYTIC = 0, 1
 
 
 class MatleapError(RuntimeError):
@@ -40,7 +41,7 @@ class ml_sim_params(C.Structure):
                 ("fd_h", C.c_double), ("max_steps", C.c_int64), ("max_reject", C.c_int32),
                 ("mode", C.c_int32), ("precision", C.c_int32), ("form", C.c_int32),
                 ("shape", C.c_int32), ("block_size", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("use_graph", C.c_int32)]
+                ("use_graph", C.c_int32), ("jacobian", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -97,11 +97,12 @@ def test_ref_bit_parity_small_counts_modes(ml, oracle, mode, x0):
 
 @pytest.mark.parametrize("mode", [0, 1])
 def test_ref_bit_parity_rejections(ml, oracle, mode):
-    # without critical reactions (n_c = 0) small counts make leaps overshoot: the
-    # negativity check rejects and halves tau
+    # without critical reactions (n_c = 0) and without the SSA switch (ssa_factor = 0)
+    # small counts make leaps overshoot: the negativity check rejects and halves tau
     crn = W.dimerisation()
-    g = run_gpu(ml, crn, 2000, [12, 5, 0], [1.5], seed=13, mode=mode, n_c=0)
-    o = run_oracle(oracle, crn, 2000, [12, 5, 0], [1.5], seed=13, mode=mode, n_c=0)
+    kw = dict(mode=mode, n_c=0, ssa_factor=0.0)
+    g = run_gpu(ml, crn, 2000, [12, 5, 0], [1.5], seed=13, **kw)
+    o = run_oracle(oracle, crn, 2000, [12, 5, 0], [1.5], seed=13, **kw)
     assert_bit_parity(g, o, f"reject mode{mode}")
     assert g["counters"][:, 3].sum() > 0
 
@@ -177,7 +178,7 @@ def test_fast_statistics_dimerisation(ml, oracle):
     g = run_gpu(ml, w.crn, w.n_traj, w.x0, w.T, seed=21, precision=ml.ML_PREC_FAST_FP32,
                 form=ml.ML_FORM_PERSISTENT, use_graph=1)
     o = run_oracle(oracle, w.crn, w.n_traj, w.x0, w.T, seed=21)
-    rows = stats_util.compare(g, o)
+    rows = stats_util.compare(g, o, g_res=stats_util.G_RESOLUTION_FAST)
     s = stats_util.summary(rows)
     assert s["holm_pass_0.01"], (s, sorted(rows, key=lambda r: r[2])[:5])
     assert (g["status"] == 0).all()
@@ -188,7 +189,7 @@ def test_fast_statistics_immigration_death_and_gene(ml, oracle):
         w = W.config(cfg, n_traj=n)
         g = run_gpu(ml, w.crn, n, w.x0, w.T, w.theta, seed=31, precision=ml.ML_PREC_FAST_FP32)
         o = run_oracle(oracle, w.crn, n, w.x0, w.T, w.theta, seed=31)
-        rows = stats_util.compare(g, o)
+        rows = stats_util.compare(g, o, g_res=stats_util.G_RESOLUTION_FAST)
         s = stats_util.summary(rows)
         assert s["holm_pass_0.01"], (cfg, s, sorted(rows, key=lambda r: r[2])[:5])
 
@@ -206,3 +207,108 @@ def test_autotune_picks_a_valid_shape(ml):
                           n_sample=8192)
     assert best.shape in (ml.ML_SHAPE_THREAD, ml.ML_SHAPE_WARP)
     assert best.block_size in (64, 128, 256)
+
+
+# ---- one trajectory per warp ------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["immigration_death", "dimerisation", "gene_expression"])
+def test_ref_warp_shape_bit_parity_small_networks(ml, oracle, name):
+    """The warp kernel keeps the same canonical order, so it matches the same oracle."""
+    w, kw = CASES[name]()
+    n = min(w.n_traj, 1000)
+    th = None if w.theta is None else w.theta[:n]
+    T = w.T[:n] if w.T.size > 1 else w.T
+    g = run_gpu(ml, w.crn, n, w.x0, T, th, seed=3, shape=ml.ML_SHAPE_WARP)
+    o = run_oracle(oracle, w.crn, n, w.x0, T, th, seed=3)
+    assert_bit_parity(g, o, name + " warp")
+
+
+def test_ref_warp_generic_and_small_counts(ml, oracle):
+    crn = _generic_network()
+    x0 = [20000, 10000, 500, 0, 300]
+    g = run_gpu(ml, crn, 600, x0, [0.5], seed=5, shape=ml.ML_SHAPE_WARP)
+    o = run_oracle(oracle, crn, 600, x0, [0.5], seed=5)
+    assert_bit_parity(g, o, "generic5 warp")
+    crn = W.dimerisation()
+    for mode, n_c, f in ((0, 10, 10.0), (1, 0, 0.0), (0, 0, 0.0), (2, 10, 10.0)):
+        g = run_gpu(ml, crn, 800, [12, 5, 0], [1.5], seed=13, mode=mode, n_c=n_c,
+                    ssa_factor=f, shape=ml.ML_SHAPE_WARP)
+        o = run_oracle(oracle, crn, 800, [12, 5, 0], [1.5], seed=13, mode=mode, n_c=n_c,
+                       ssa_factor=f)
+        assert_bit_parity(g, o, f"dimer warp mode{mode}")
+
+
+def test_ref_random_crn_50x100(ml, oracle):
+    """The large random network (50 species, 100 reactions, 10 reversible pairs) on a short
+    horizon: explicit, implicit (50x50 Newton) and SSA steps, bit-identical."""
+    w = W.config(3, n_traj=48)
+    g = run_gpu(ml, w.crn, 48, w.x0, [0.05], seed=9, base=1000)
+    o = run_oracle(oracle, w.crn, 48, w.x0, [0.05], seed=9, base=1000)
+    assert_bit_parity(g, o, "random_crn")
+    c = g["counters"].sum(0)
+    assert c[1] > 0 and c[2] > 0  # implicit leaps and SSA firings both occurred
+
+
+def test_fast_warp_statistics_dimerisation(ml, oracle):
+    w = W.config(1, n_traj=20000)
+    g = run_gpu(ml, w.crn, w.n_traj, w.x0, w.T, seed=22, precision=ml.ML_PREC_FAST_FP32,
+                shape=ml.ML_SHAPE_WARP, form=ml.ML_FORM_PERSISTENT)
+    o = run_oracle(oracle, w.crn, w.n_traj, w.x0, w.T, seed=22)
+    s = stats_util.summary(stats_util.compare(g, o, g_res=stats_util.G_RESOLUTION_FAST))
+    assert s["holm_pass_0.01"], s
+
+
+def test_fast_random_crn_statistics(ml, oracle):
+    w = W.config(3, n_traj=400)
+    g = run_gpu(ml, w.crn, 400, w.x0, [0.02], seed=23, precision=ml.ML_PREC_FAST_FP32,
+                form=ml.ML_FORM_PERSISTENT)
+    o = run_oracle(oracle, w.crn, 400, w.x0, [0.02], seed=23)
+    s = stats_util.summary(stats_util.compare(g, o, g_res=stats_util.G_RESOLUTION_FAST))
+    assert s["holm_pass_0.01"], s
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_ref_bit_parity_analytic_jacobian(ml, oracle, shape):
+    """The exact (symbolic) Jacobian option: bit-identical to the oracle's exact
+    Jacobian, in both kernel shapes."""
+    w = W.config(1, n_traj=3000)
+    g = run_gpu(ml, w.crn, w.n_traj, w.x0, w.T, seed=17, jacobian=1, shape=shape)
+    o = run_oracle(oracle, w.crn, w.n_traj, w.x0, w.T, seed=17, jacobian=1)
+    assert_bit_parity(g, o, f"analytic shape{shape}")
+    assert g["counters"][:, 1].sum() > 0
+    crn = _generic_network()
+    x0 = [20000, 10000, 500, 0, 300]
+    g = run_gpu(ml, crn, 600, x0, [0.5], seed=5, jacobian=1, shape=shape)
+    o = run_oracle(oracle, crn, 600, x0, [0.5], seed=5, jacobian=1)
+    assert_bit_parity(g, o, f"generic analytic shape{shape}")
+
+
+def test_ref_random_crn_analytic_jacobian(ml, oracle):
+    w = W.config(3, n_traj=32)
+    g = run_gpu(ml, w.crn, 32, w.x0, [0.05], seed=19, jacobian=1)
+    o = run_oracle(oracle, w.crn, 32, w.x0, [0.05], seed=19, jacobian=1)
+    assert_bit_parity(g, o, "random_crn analytic")
+
+
+@pytest.mark.parametrize("mu", [3.0, 9.5, 50.0, 1.2e4, 1e6, 3e7])
+def test_fast_poisson_sampler_law(ml, oracle, mu):
+    """0 -> A at rate mu over T = 1 from A = 0: no species bounds the leap, so each
+    trajectory is one leap to T and X(T) is a single Poisson(mu) draw of the kernel's
+    sampler (inversion below 10, PTRS above).  Fast precision against scipy's Poisson law."""
+    from scipy import stats
+    crn = W._crn("source", 1, [({}, {0: 1}, mu)])
+    n = 100_000
+    for shape in (1, 2):
+        g = run_gpu(ml, crn, n, [0], [1.0], seed=29, precision=ml.ML_PREC_FAST_FP32,
+                    shape=shape, form=ml.ML_FORM_PERSISTENT)
+        assert (g["counters"][:, 0] == 1).all()
+        X = g["X"][:, 0].astype(np.float64)
+        assert abs(X.mean() - mu) < 5 * np.sqrt(mu / n)
+        se_var = np.sqrt((mu + 2 * mu * mu) / n)
+        assert abs(X.var() - mu) < 5 * se_var
+        lo, hi = stats.poisson.ppf([1e-4, 1 - 1e-4], mu)
+        edges = np.unique(np.round(np.linspace(lo, hi + 1, 30)))
+        obs = np.histogram(X, np.concatenate([[-np.inf], edges[1:-1], [np.inf]]))[0]
+        p = np.diff(np.concatenate([[0.0], stats.poisson.cdf(edges[1:-1] - 1, mu), [1.0]]))
+        keep = p * n > 5
+        assert stats.chisquare(obs[keep], p[keep] * n * obs[keep].sum() / (p[keep] * n).sum()).pvalue > 1e-4
