@@ -181,6 +181,32 @@ int ml_autotune(ml_model* model, int64_t n_traj, const double* theta, const int6
                 const ml_sim_params* p, uint64_t seed, int64_t n_sample,
                 ml_sim_params* best, void* cuda_stream);
 
+/* Allocation-free variant of ml_simulate, for callers that cannot let a library allocate
+ * device memory: code running under a device-memory pool owned by a host framework (a
+ * deep-learning runtime, an MPS client with a capped budget), latency-bound loops that
+ * cannot afford cudaMalloc's implicit synchronization, and code that must not take the
+ * CUDA allocator's lock.  The paper has no counterpart; this is a deployment interface.
+ *   Same arguments and results as ml_simulate (all buffers caller-owned device memory).
+ *   Always runs the persistent refill kernel, one trajectory per thread, in p's precision
+ *   (p->form and p->use_graph are ignored).
+ *   Its only scratch (the work-queue counter and a copy of the model tables) is a fixed
+ *   4 KiB device array inside the library, reserved on every GPU that loads it until the
+ *   process exits; at most 3840 bytes of model tables fit, i.e. at most 8 species and 16
+ *   reactions.  Larger models are rejected with ML_ERR_ARG and a message naming the size.
+ *   The first call on a device looks up the array's device address (with that device
+ *   current), so make that first call before any stream capture.
+ *   Every call reuses the same array and overwrites what the previous call left there:
+ *   calls whose kernels overlap on the GPU (other streams, other threads) race and must
+ *   be serialized by the caller.
+ *   Makes no cudaMalloc, cudaFree or other allocating call.
+ * Errors: as ml_simulate, plus ML_ERR_UNSUPPORTED for models that need one warp per
+ * trajectory. */
+int ml_simulate_noalloc(const ml_model* model, int64_t n_traj, const double* theta,
+                        const int64_t* x0, int32_t x0_per_traj, const double* T,
+                        int32_t T_per_traj, const ml_sim_params* p, uint64_t seed,
+                        uint64_t traj_id_base, int64_t* X_out, int64_t* r_out, double* G_out,
+                        uint32_t* status_out, int64_t* counters_out, void* cuda_stream);
+
 /* Number of kernel launches the last ml_simulate/ml_simulate_host call on this model
  * issued (a graph replay counts its kernel nodes), or ML_ERR_ARG. */
 int64_t ml_model_last_launch_count(const ml_model* model);

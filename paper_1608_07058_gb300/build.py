@@ -35,6 +35,7 @@ def _units():
         u.append(("kern_warp.cu", f"kw_{'fast' if fast else 'ref'}.o",
                   [f"-DML_FAST={fast}"] + ([] if fast else ["-fmad=false"])))
     u.append(("api.cu", "api.o", []))
+    u.append(("noalloc.cu", "noalloc.o", []))
     return u
 
 

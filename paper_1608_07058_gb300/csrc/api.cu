@@ -83,6 +83,9 @@ struct ml_model {
   std::mutex mu;
   std::map<int, DeviceState> dev;
   int64_t last_launches = 0;
+  int thread_variant = -1;                // smallest thread variant holding the model
+  std::vector<uint8_t> host_thread_tables;  // its tables (for the allocation-free path)
+  size_t warp_table_bytes = 0;
 };
 
 namespace {
@@ -473,6 +476,76 @@ int check_sizes(const ml_model* m, int64_t n_traj, uint64_t id_base) {
 
 }  // namespace
 
+namespace mlk {
+
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+int noalloc_prepare(const ml_model* m, int64_t n_traj, const double* theta, const int64_t* x0,
+                    int32_t x0_per_traj, const double* T, int32_t T_per_traj,
+                    const void* params, uint64_t seed, uint64_t id_base, int64_t* X,
+                    int64_t* r, double* G, uint32_t* status, int64_t* counters,
+                    size_t scratch_table_max, NoAllocLaunch* out) {
+  int rc = check_sizes(m, n_traj, id_base);
+  if (rc != ML_OK) return rc;
+  ml_sim_params p;
+  if (params) p = *static_cast<const ml_sim_params*>(params);
+  else ml_default_params(&p);
+  p.form = ML_FORM_PERSISTENT;
+  p.use_graph = 0;
+  rc = check_params(p);
+  if (rc != ML_OK) return rc;
+  const size_t need = m->thread_variant >= 0 ? m->host_thread_tables.size() : m->warp_table_bytes;
+  if (need > scratch_table_max)
+    return fail(ML_ERR_ARG,
+                "model %dx%d needs %zu bytes of model tables; the allocation-free entry point "
+                "holds at most %zu (one trajectory per thread: at most 8 species and 16 "
+                "reactions)",
+                m->N, m->M, need, scratch_table_max);
+  if (m->thread_variant < 0 || p.shape == ML_SHAPE_WARP)
+    return fail(ML_ERR_UNSUPPORTED, "the allocation-free entry point runs one trajectory per thread only");
+  const struct {
+    const void* ptr;
+    const char* name;
+    bool required;
+  } ptrs[] = {{theta, "theta", false}, {x0, "x0", true},      {T, "T", true},
+              {X, "X_out", true},      {r, "r_out", true},    {G, "G_out", true},
+              {status, "status_out", true}, {counters, "counters_out", false}};
+  if (n_traj > 0) {
+    for (const auto& q : ptrs) {
+      if (!q.ptr) {
+        if (q.required) return fail(ML_ERR_ARG, "%s is NULL", q.name);
+        continue;
+      }
+      if (!is_device_pointer(q.ptr))
+        return fail(ML_ERR_ARG, "%s is not device memory of the current device", q.name);
+    }
+  }
+  int dev = 0, sms = 0;
+  ML_CUDA_TRY(cudaGetDevice(&dev));
+  ML_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  out->entry = thread_entry(p.precision, m->thread_variant);
+  if (!out->entry.kernel) return fail(ML_ERR_UNSUPPORTED, "no kernel built for this precision");
+  out->host_tables = m->host_thread_tables.data();
+  out->table_bytes = m->host_thread_tables.size();
+  const int block = p.block_size ? p.block_size : 128;
+  int per_sm = p.ctas_per_sm;
+  if (per_sm == 0) {
+    int occ = 0;
+    ML_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, out->entry.kernel, block, 0));
+    per_sm = occ > 0 ? occ : 1;
+  }
+  int64_t grid = (int64_t)sms * per_sm;
+  const int64_t needed = (n_traj + block - 1) / block;
+  grid = std::max<int64_t>(1, std::min(grid, needed));
+  out->grid = (int)grid;
+  out->block = block;
+  fill_args(m, p, n_traj, theta, x0, x0_per_traj, T, T_per_traj, seed, id_base, X, r, G,
+            status, counters, &out->args);
+  return ML_OK;
+}
+
+}  // namespace mlk
+
 extern "C" {
 
 int ml_default_params(ml_sim_params* p) {
@@ -573,6 +646,9 @@ int ml_model_create(int32_t N, int32_t M, const int32_t* ord, const int32_t* nu,
       }
     }
   }
+  m->thread_variant = thread_variant_for(*m);
+  if (m->thread_variant >= 0) m->host_thread_tables = thread_tables(m->thread_variant, *m);
+  m->warp_table_bytes = (sizeof(mlk::WarpModel) + 15) / 16 * 16;
   *out = m.release();
   return ML_OK;
 }

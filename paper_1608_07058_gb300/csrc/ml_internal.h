@@ -130,5 +130,27 @@ KernelEntry warp_entry_fast();
 // Dynamic shared memory of the warp kernel for a CTA of `warps` warps.
 size_t warp_smem_bytes(int warps, int N, int M, int precision);
 
+// Launch description for the allocation-free entry point: everything is validated and
+// chosen by the host API without touching device memory; the caller copies host_tables
+// into its own scratch and fills args.queue.
+struct NoAllocLaunch {
+  KernelEntry entry;
+  const void* host_tables;  // built at model creation, lives as long as the model
+  size_t table_bytes;
+  int grid, block;
+  SimArgs args;
+};
+}  // namespace mlk
+
+struct ml_model;
+namespace mlk {
+// Returns ML_OK and fills *out, or an ML_ERR_* code (message set).  `scratch_table_max`
+// is the room for model tables in the caller's scratch.
+int noalloc_prepare(const ml_model* m, int64_t n_traj, const double* theta, const int64_t* x0,
+                    int32_t x0_per_traj, const double* T, int32_t T_per_traj,
+                    const void* params, uint64_t seed, uint64_t id_base, int64_t* X,
+                    int64_t* r, double* G, uint32_t* status, int64_t* counters,
+                    size_t scratch_table_max, NoAllocLaunch* out);
+int set_error(int code, const char* msg);
 
 }  // namespace mlk

@@ -71,6 +71,7 @@ def lib():
                C.c_uint64, v, v, v, v, v, v]
         L.ml_simulate.argtypes = sim
         L.ml_simulate_host.argtypes = sim
+        L.ml_simulate_noalloc.argtypes = sim
         L.ml_autotune.argtypes = [v, C.c_int64, v, v, C.c_int32, v, C.c_int32,
                                   P(ml_sim_params), C.c_uint64, C.c_int64, P(ml_sim_params), v]
         _lib = L
@@ -178,6 +179,20 @@ def ml_simulate(model: Model, n_traj: int, x0, T, theta=None, params: Optional[m
                              seed, traj_id_base, _ptr(out["X"]), _ptr(out["r"]), _ptr(out["G"]),
                              _ptr(out["status"]), _ptr(out.get("counters")),
                              _stream_handle(stream)))
+    return out
+
+
+def ml_simulate_noalloc(model: Model, n_traj: int, x0, T, theta=None,
+                        params: Optional[ml_sim_params] = None, seed: int = 0,
+                        traj_id_base: int = 0, out: dict = None, stream=None) -> dict:
+    """Allocation-free entry point: like ml_simulate with caller-allocated `out` (dict of
+    CUDA tensors X, r, G, status[, counters]); the library allocates no device memory."""
+    p = params if params is not None else ml_default_params()
+    _check(lib().ml_simulate_noalloc(C.c_void_p(model.handle), n_traj, _ptr(theta), _ptr(x0),
+                                     int(x0.dim() == 2), _ptr(T), int(T.numel() > 1),
+                                     C.byref(p), seed, traj_id_base, _ptr(out["X"]),
+                                     _ptr(out["r"]), _ptr(out["G"]), _ptr(out["status"]),
+                                     _ptr(out.get("counters")), _stream_handle(stream)))
     return out
 
 
