@@ -299,7 +299,8 @@ def run_ours(args):
             "config": {"workload": workload_name(w), "form": "persistent refill kernel, CUDA graph, autotuned",
                        "precision": "FP32 propensities/tau/Poisson, FP64 t/G/Newton",
                        "jacobian": args.jacobian,
-                       "shape": {"shape": "thread" if fast.shape == ml.ML_SHAPE_THREAD else ("warp" if fast.shape == ml.ML_SHAPE_WARP else "auto"),
+                       "shape": {"shape": {ml.ML_SHAPE_THREAD: "thread", ml.ML_SHAPE_WARP: "warp",
+                                           ml.ML_SHAPE_THREAD_OCC: "thread (128-register build)"}.get(fast.shape, "auto"),
                                  "block_size": fast.block_size, "ctas_per_sm": fast.ctas_per_sm},
                        "l2": "flushed between steps (256 MB write)"},
             "leap_steps_per_s": leap_steps / (ms_fast / 1e3),

@@ -32,6 +32,10 @@ def _units():
         for v in range(N_THREAD_VARIANTS):
             u.append(("kern_thread.cu", f"kt_{'fast' if fast else 'ref'}_{v}.o",
                       [f"-DML_FAST={fast}", f"-DML_VARIANT={v}"] + ([] if fast else ["-fmad=false"])))
+        if fast:
+            for v in range(N_THREAD_VARIANTS):
+                u.append(("kern_thread.cu", f"kt_fastocc_{v}.o",
+                          ["-DML_FAST=1", f"-DML_VARIANT={v}", "-DML_THREAD_MIN_BLOCKS=2"]))
         u.append(("kern_warp.cu", f"kw_{'fast' if fast else 'ref'}.o",
                   [f"-DML_FAST={fast}"] + ([] if fast else ["-fmad=false"])))
     u.append(("api.cu", "api.o", []))

@@ -1,6 +1,8 @@
 // One thread-per-trajectory kernel variant, selected at compile time:
 //   ML_FAST = 0: reference precision (compile with -fmad=false), 1: fast precision;
-//   ML_VARIANT: index into the (species, reactions) capacity table.
+//   ML_VARIANT: index into the (species, reactions) capacity table;
+//   ML_THREAD_MIN_BLOCKS = 2 (fast only): the 128-register build (more resident warps,
+//   some spilling), offered to the autotuner as a separate shape.
 #include "thread_core.cuh"
 
 #ifndef ML_VARIANT
@@ -10,7 +12,10 @@
 #define ML_CAT(a, b, c) ML_CAT_(a, b, c)
 
 namespace mlk {
-#if ML_FAST
+#if ML_FAST && ML_THREAD_MIN_BLOCKS == 2
+using Prec = PrecFast;
+#define ML_PNAME fastocc
+#elif ML_FAST
 using Prec = PrecFast;
 #define ML_PNAME fast
 #else

@@ -48,10 +48,11 @@ __device__ __forceinline__ R comb_factor(R v, int m) {
 }
 
 // d/dv C(v, m): 1, v - 1/2, (3 v^2 - 6 v + 2) / 6, in this operation order.
-__device__ __forceinline__ double comb_factor_deriv(double v, int m) {
-  if (m == 1) return 1.0;
-  if (m == 2) return v - 0.5;
-  return ((3.0 * (v * v) - 6.0 * v) + 2.0) / 6.0;
+template <class T>
+__device__ __forceinline__ T comb_factor_deriv(T v, int m) {
+  if (m == 1) return T(1);
+  if (m == 2) return v - T(0.5);
+  return ((T(3) * (v * v) - T(6) * v) + T(2)) / T(6);
 }
 
 // Highest-order-reaction factor h_s (Cao 2006) from the species' flags and count.
@@ -233,13 +234,14 @@ struct ThreadTraj {
   }
 
   // exact d g_j / d y_q: the product with species q's factor replaced by its derivative
-  __device__ static __forceinline__ double g_real_deriv(const Model& md, int j,
-                                                        const double (&y)[NM], int q) {
-    double v = 1.0;
+  template <class T>
+  __device__ static __forceinline__ T g_real_deriv(const Model& md, int j, const T (&y)[NM],
+                                                   int q) {
+    T v = T(1);
 #pragma unroll
     for (int s = 0; s < NM; ++s) {
       const int m = md.ord[j][s];
-      if (m != 0) v = v * (s == q ? comb_factor_deriv(y[s], m) : comb_factor<double>(y[s], m));
+      if (m != 0) v = v * (s == q ? comb_factor_deriv<T>(y[s], m) : comb_factor<T>(y[s], m));
     }
     return v;
   }
@@ -284,8 +286,11 @@ struct ThreadTraj {
   }
 
   // Implicit leap (Rathinam 2003): solve y = c + tau sum_j nu_j a_j(y) over the
-  // non-critical reactions by Newton with a forward-difference Jacobian, Gaussian
-  // elimination with partial pivoting and column-oriented back substitution.
+  // non-critical reactions by Newton's method: residual, iterate and stopping test in
+  // FP64; the Jacobian (forward differences or exact) assembled and factorized by Gaussian
+  // elimination with partial pivoting and column-oriented back substitution in the
+  // working precision R (FP64 in reference precision; FP32 in fast precision, where an
+  // approximate Jacobian changes only the rate of convergence, not the FP64 root).
   // Returns 0 converged, 1 not converged, 2 singular.
   __device__ static int implicit_solve(const Model& md, const R (&th)[MM],
                                        const long long (&x)[NM], uint32_t nc,
@@ -305,11 +310,12 @@ struct ThreadTraj {
       c[s] = acc;
       y[s] = (double)x[s];
     }
+    const R taur = (R)tau;
     for (int it = 0; it < maxit; ++it) {
       double ay[MM];
 #pragma unroll
       for (int j = 0; j < MM; ++j) ay[j] = (double)th[j] * g_real(md, j, y);
-      double A[NM][NM], b[NM];
+      R A[NM][NM], b[NM];
 #pragma unroll
       for (int s = 0; s < NM; ++s) {
         double acc = 0.0;
@@ -318,17 +324,20 @@ struct ThreadTraj {
           const int v = md.nu[j][s];
           if (((nc >> j) & 1u) && v != 0) acc = acc + (double)v * ay[j];
         }
-        b[s] = -((y[s] - c[s]) - tau * acc);
+        b[s] = (R)(-((y[s] - c[s]) - tau * acc));
       }
+      R yr[NM];
+#pragma unroll
+      for (int s = 0; s < NM; ++s) yr[s] = (R)y[s];
 #pragma unroll
       for (int q = 0; q < NM; ++q) {
-        double Dq[MM];
+        R Dq[MM];
         if (analytic) {
 #pragma unroll
           for (int j = 0; j < MM; ++j)
             Dq[j] = (((nc >> j) & 1u) && md.ord[j][q] != 0)
-                        ? (double)th[j] * g_real_deriv(md, j, y, q)
-                        : 0.0;
+                        ? th[j] * g_real_deriv<R>(md, j, yr, q)
+                        : R(0);
         } else {
           const double aq = fabs(y[q]);
           const double h = fd_h * (aq > 1.0 ? aq : 1.0);
@@ -340,26 +349,25 @@ struct ThreadTraj {
 #pragma unroll
           for (int j = 0; j < MM; ++j)
             Dq[j] = (((nc >> j) & 1u) && md.ord[j][q] != 0)
-                        ? ((double)th[j] * g_real(md, j, yq) - ay[j]) / he
-                        : 0.0;
+                        ? (R)(((double)th[j] * g_real(md, j, yq) - ay[j]) / he)
+                        : R(0);
         }
 #pragma unroll
         for (int s = 0; s < NM; ++s) {
-          double acc = 0.0;
+          R acc = R(0);
 #pragma unroll
           for (int j = 0; j < MM; ++j) {
             const int v = md.nu[j][s];
-            if (((nc >> j) & 1u) && v != 0 && md.ord[j][q] != 0)
-              acc = acc + (double)v * Dq[j];
+            if (((nc >> j) & 1u) && v != 0 && md.ord[j][q] != 0) acc = acc + (R)v * Dq[j];
           }
-          A[s][q] = (s == q ? 1.0 : 0.0) - tau * acc;
+          A[s][q] = (s == q ? R(1) : R(0)) - taur * acc;
         }
       }
       // elimination with partial pivoting (row swaps by compile-time selects)
 #pragma unroll
       for (int k = 0; k < NM; ++k) {
         int piv = k;
-        double best = fabs(A[k][k]);
+        R best = fabs(A[k][k]);
 #pragma unroll
         for (int i = k + 1; i < NM; ++i) {
           if (fabs(A[i][k]) > best) {
@@ -367,30 +375,30 @@ struct ThreadTraj {
             piv = i;
           }
         }
-        if (best == 0.0) return 2;
+        if (best == R(0)) return 2;
 #pragma unroll
         for (int i = k + 1; i < NM; ++i) {
           if (i == piv) {
 #pragma unroll
             for (int cc = 0; cc < NM; ++cc) {
-              const double tmp = A[k][cc];
+              const R tmp = A[k][cc];
               A[k][cc] = A[i][cc];
               A[i][cc] = tmp;
             }
-            const double tb = b[k];
+            const R tb = b[k];
             b[k] = b[i];
             b[i] = tb;
           }
         }
 #pragma unroll
         for (int i = k + 1; i < NM; ++i) {
-          const double l = A[i][k] / A[k][k];
+          const R l = A[i][k] / A[k][k];
 #pragma unroll
           for (int cc = k + 1; cc < NM; ++cc) A[i][cc] = A[i][cc] - l * A[k][cc];
           b[i] = b[i] - l * b[k];
         }
       }
-      double d[NM];
+      R d[NM];
 #pragma unroll
       for (int i = NM - 1; i >= 0; --i) {
         d[i] = b[i] / A[i][i];
@@ -400,8 +408,9 @@ struct ThreadTraj {
       double dmax = 0.0, ymax = 0.0;
 #pragma unroll
       for (int s = 0; s < NM; ++s) {
-        y[s] = y[s] + d[s];
-        if (fabs(d[s]) > dmax) dmax = fabs(d[s]);
+        const double ds = (double)d[s];
+        y[s] = y[s] + ds;
+        if (fabs(ds) > dmax) dmax = fabs(ds);
         if (fabs(y[s]) > ymax) ymax = fabs(y[s]);
       }
       if (dmax <= tol * (ymax > 1.0 ? ymax : 1.0)) return 0;
@@ -718,12 +727,16 @@ struct ThreadTraj {
   }
 };
 
+#ifndef ML_THREAD_MIN_BLOCKS
+#define ML_THREAD_MIN_BLOCKS 1  // 2: a 128-register build with twice the resident warps
+#endif
+
 // Kernel: stage the model tables once per CTA, then simulate.  Plain form (queue null):
 // thread i runs trajectory i.  Persistent form: each thread claims trajectory indices
 // from the device queue until none is left, so a thread that finishes early
 // immediately refills its slot.
 template <int NM, int MM, class P>
-__global__ void __launch_bounds__(256) k_thread(const ThreadModel<NM, MM>* __restrict__ gmd,
+__global__ void __launch_bounds__(256, ML_THREAD_MIN_BLOCKS) k_thread(const ThreadModel<NM, MM>* __restrict__ gmd,
                                                 const SimArgs args) {
   __shared__ ThreadModel<NM, MM> smd;
   __shared__ uint64_t mbar;

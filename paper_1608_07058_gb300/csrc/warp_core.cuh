@@ -20,29 +20,32 @@ namespace mlk {
 constexpr int kRPL = kWarpMaxM / 32;  // reactions per lane
 constexpr int kSPL = kWarpMaxN / 32;  // species per lane
 
-// Per-warp shared-memory slab; offsets depend on the model size.
+// Per-warp shared-memory slab; offsets depend on the model size and on the working
+// precision R (rbytes = sizeof(R)): the Newton matrix, right-hand side and derivatives are
+// in R, the iterate and its propensities in FP64.
 struct WarpSlab {
   long long* x;   // [N] state
   long long* xn;  // [N] proposed state
   long long* K;   // [M] firings of the current leap (Poisson draws before the solve)
   double* y;      // [N] Newton iterate
-  double* b;      // [N] right-hand side / update
   double* ay;     // [M] propensities at y
-  double* D;      // [M][3] forward differences by reactant slot
-  double* J;      // [N][N] Newton matrix
+  void* b;        // [N] right-hand side / update (R)
+  void* D;        // [M][3] Jacobian entries by reactant slot (R)
+  void* J;        // [N][N] Newton matrix (R)
   void* a;        // [M] propensities (R)
   void* ac;       // [M] critical propensities (R)
 };
 
 __host__ __device__ inline size_t warp_slab_bytes(int N, int M, int rbytes) {
   size_t b = 0;
-  b += 8 * (size_t)N * 2;          // x, xn
-  b += 8 * (size_t)M;              // K
-  b += 8 * (size_t)N * 2;          // y, b
-  b += 8 * (size_t)M;              // ay
-  b += 24 * (size_t)M;             // D
-  b += 8 * (size_t)N * (size_t)N;  // J
-  b += (size_t)rbytes * M * 2;     // a, ac
+  b += 8 * (size_t)N * 2;                      // x, xn
+  b += 8 * (size_t)M;                          // K
+  b += 8 * (size_t)N;                          // y
+  b += 8 * (size_t)M;                          // ay
+  b += (size_t)rbytes * N;                     // b
+  b += (size_t)rbytes * 3 * M;                 // D
+  b += (size_t)rbytes * (size_t)N * (size_t)N; // J
+  b += (size_t)rbytes * M * 2;                 // a, ac
   return (b + 15) / 16 * 16;
 }
 
@@ -56,14 +59,14 @@ __device__ inline WarpSlab carve_slab(char* p, int N, int M, int rbytes) {
   p += 8 * M;
   s.y = reinterpret_cast<double*>(p);
   p += 8 * N;
-  s.b = reinterpret_cast<double*>(p);
-  p += 8 * N;
   s.ay = reinterpret_cast<double*>(p);
   p += 8 * M;
-  s.D = reinterpret_cast<double*>(p);
-  p += 24 * M;
-  s.J = reinterpret_cast<double*>(p);
-  p += 8 * (size_t)N * N;
+  s.b = p;
+  p += (size_t)rbytes * N;
+  s.D = p;
+  p += (size_t)rbytes * 3 * M;
+  s.J = p;
+  p += (size_t)rbytes * (size_t)N * N;
   s.a = p;
   p += (size_t)rbytes * M;
   s.ac = p;
@@ -209,12 +212,18 @@ struct WarpTraj {
     }
   }
 
-  // Implicit solve on the per-warp slab.  Returns 0 converged, 1 not converged, 2 singular.
+  // Implicit solve on the per-warp slab: residual, iterate and stopping test in FP64;
+  // Jacobian, elimination and back substitution in R (FP64 in reference precision).
+  // Returns 0 converged, 1 not converged, 2 singular.
   __device__ static int implicit_solve(const WarpModel& md, const WarpSlab& sl,
                                        const R (&th)[kRPL], const uint32_t (&nc)[kRPL],
                                        const R* a, double tau, double tol, int maxit,
                                        double fd_h, bool analytic, int lane) {
     const int N = md.N, M = md.M;
+    R* const Jm = static_cast<R*>(sl.J);
+    R* const bv = static_cast<R*>(sl.b);
+    R* const Dm = static_cast<R*>(sl.D);
+    const R taur = (R)tau;
     double c[kSPL];
 #pragma unroll
     for (int q = 0; q < kSPL; ++q) {
@@ -239,7 +248,7 @@ struct WarpTraj {
         if (j < M) sl.ay[j] = (double)th[q] * g_real(md, j, sl.y, -1, 0.0);
       }
       __syncwarp();
-      // right-hand side and forward differences
+      // right-hand side and Jacobian entries
 #pragma unroll
       for (int q = 0; q < kSPL; ++q) {
         const int s = lane + 32 * q;
@@ -249,7 +258,7 @@ struct WarpTraj {
             const int j = md.sp_j[e];
             if (bit(nc, j)) acc = acc + (double)md.sp_nu[e] * sl.ay[j];
           }
-          sl.b[s] = -((sl.y[s] - c[q]) - tau * acc);
+          bv[s] = (R)(-((sl.y[s] - c[q]) - tau * acc));
         }
       }
 #pragma unroll
@@ -258,16 +267,16 @@ struct WarpTraj {
         if (j < M) {
           const int nr = md.nreact[j];
           for (int k = 0; k < 3; ++k) {
-            double dv = 0.0;
+            R dv = R(0);
             if (k < nr && bit(nc, j)) {
               if (analytic) {
-                double v = 1.0;
+                R v = R(1);
                 for (int kk = 0; kk < nr; ++kk) {
-                  const double ys = sl.y[md.rsp[j][kk]];
+                  const R ys = (R)sl.y[md.rsp[j][kk]];
                   const int m = md.rmul[j][kk];
-                  v = v * (kk == k ? comb_factor_deriv(ys, m) : comb_factor<double>(ys, m));
+                  v = v * (kk == k ? comb_factor_deriv<R>(ys, m) : comb_factor<R>(ys, m));
                 }
-                dv = (double)th[q] * v;
+                dv = th[q] * v;
               } else {
                 const int sq = md.rsp[j][k];
                 const double yq = sl.y[sq];
@@ -275,10 +284,10 @@ struct WarpTraj {
                 const double h = fd_h * (aq > 1.0 ? aq : 1.0);
                 const double yp = yq + h;
                 const double he = yp - yq;
-                dv = ((double)th[q] * g_real(md, j, sl.y, sq, yp) - sl.ay[j]) / he;
+                dv = (R)(((double)th[q] * g_real(md, j, sl.y, sq, yp) - sl.ay[j]) / he);
               }
             }
-            sl.D[j * 3 + k] = dv;
+            Dm[j * 3 + k] = dv;
           }
         }
       }
@@ -288,28 +297,28 @@ struct WarpTraj {
       for (int q = 0; q < kSPL; ++q) {
         const int s = lane + 32 * q;
         if (s < N) {
-          double* row = sl.J + (size_t)s * N;
-          for (int cc = 0; cc < N; ++cc) row[cc] = 0.0;
+          R* row = Jm + (size_t)s * N;
+          for (int cc = 0; cc < N; ++cc) row[cc] = R(0);
           for (int e = md.sp_ptr[s]; e < md.sp_ptr[s + 1]; ++e) {
             const int j = md.sp_j[e];
             if (!bit(nc, j)) continue;
-            const double v = (double)md.sp_nu[e];
+            const R v = (R)md.sp_nu[e];
             const int nr = md.nreact[j];
             for (int k = 0; k < nr; ++k) {
               const int qq = md.rsp[j][k];
-              row[qq] = row[qq] + v * sl.D[j * 3 + k];
+              row[qq] = row[qq] + v * Dm[j * 3 + k];
             }
           }
-          for (int cc = 0; cc < N; ++cc) row[cc] = (s == cc ? 1.0 : 0.0) - tau * row[cc];
+          for (int cc = 0; cc < N; ++cc) row[cc] = (s == cc ? R(1) : R(0)) - taur * row[cc];
         }
       }
       __syncwarp();
       // Gaussian elimination with partial pivoting (largest |pivot|, lowest row on ties)
       for (int k = 0; k < N; ++k) {
-        double best = -1.0;
+        R best = R(-1);
         int piv = N;
         for (int i = k + lane; i < N; i += 32) {
-          const double v = fabs(sl.J[(size_t)i * N + k]);
+          const R v = fabs(Jm[(size_t)i * N + k]);
           if (v > best) {
             best = v;
             piv = i;
@@ -317,43 +326,43 @@ struct WarpTraj {
         }
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) {
-          const double ob = __shfl_xor_sync(0xffffffffu, best, d);
+          const R ob = __shfl_xor_sync(0xffffffffu, best, d);
           const int op = __shfl_xor_sync(0xffffffffu, piv, d);
           if (ob > best || (ob == best && op < piv)) {
             best = ob;
             piv = op;
           }
         }
-        if (!(best > 0.0) || piv >= N) return 2;  // zero or non-finite column: singular
+        if (!(best > R(0)) || piv >= N) return 2;  // zero or non-finite column: singular
         if (piv != k) {
           for (int cc = lane; cc < N; cc += 32) {
-            const double t = sl.J[(size_t)k * N + cc];
-            sl.J[(size_t)k * N + cc] = sl.J[(size_t)piv * N + cc];
-            sl.J[(size_t)piv * N + cc] = t;
+            const R t = Jm[(size_t)k * N + cc];
+            Jm[(size_t)k * N + cc] = Jm[(size_t)piv * N + cc];
+            Jm[(size_t)piv * N + cc] = t;
           }
           if (lane == 0) {
-            const double t = sl.b[k];
-            sl.b[k] = sl.b[piv];
-            sl.b[piv] = t;
+            const R t = bv[k];
+            bv[k] = bv[piv];
+            bv[piv] = t;
           }
         }
         __syncwarp();
-        const double pk = sl.J[(size_t)k * N + k];
-        const double bk = sl.b[k];
+        const R pk = Jm[(size_t)k * N + k];
+        const R bk = bv[k];
         for (int i = k + 1 + lane; i < N; i += 32) {
-          const double l = sl.J[(size_t)i * N + k] / pk;
+          const R l = Jm[(size_t)i * N + k] / pk;
           for (int cc = k + 1; cc < N; ++cc)
-            sl.J[(size_t)i * N + cc] = sl.J[(size_t)i * N + cc] - l * sl.J[(size_t)k * N + cc];
-          sl.b[i] = sl.b[i] - l * bk;
+            Jm[(size_t)i * N + cc] = Jm[(size_t)i * N + cc] - l * Jm[(size_t)k * N + cc];
+          bv[i] = bv[i] - l * bk;
         }
         __syncwarp();
       }
       // column-oriented back substitution
       for (int i = N - 1; i >= 0; --i) {
-        const double di = sl.b[i] / sl.J[(size_t)i * N + i];
+        const R di = bv[i] / Jm[(size_t)i * N + i];
         __syncwarp();
-        for (int rr = lane; rr < i; rr += 32) sl.b[rr] = sl.b[rr] - sl.J[(size_t)rr * N + i] * di;
-        if (lane == 0) sl.b[i] = di;
+        for (int rr = lane; rr < i; rr += 32) bv[rr] = bv[rr] - Jm[(size_t)rr * N + i] * di;
+        if (lane == 0) bv[i] = di;
         __syncwarp();
       }
       double dmax = 0.0, ymax = 0.0;
@@ -361,7 +370,7 @@ struct WarpTraj {
       for (int q = 0; q < kSPL; ++q) {
         const int s = lane + 32 * q;
         if (s < N) {
-          const double d = sl.b[s];
+          const double d = (double)bv[s];
           const double yn = sl.y[s] + d;
           sl.y[s] = yn;
           dmax = fabs(d) > dmax ? fabs(d) : dmax;
