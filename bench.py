@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--jacobian", choices=["fd", "analytic"], default="analytic",
                     help="Jacobian of the implicit solve, same for both forms")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=4.0,
+                    help="arrival window of the serving mix (0 = skip it)")
     ap.add_argument("--ncu", action="store_true",
                     help="skip the CPU leg, autotune, e2e and clocks (for profiler runs)")
     return ap.parse_args()
@@ -190,6 +192,85 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------
+# serving mix: continuous batching against one request per launch
+# ---------------------------------------------------------------------------------
+def run_serving(ml, seconds, rate_hz=200.0, seed=11, max_inflight=8, budget=8 << 30):
+    import threading
+    import numpy as np
+    from paper_1608_07058_gb300 import workloads as W
+    n_req = max(1, int(round(seconds * rate_hz)))
+    reqs = W.serving_requests(n_req, seed=seed, rate_hz=rate_hz)
+    models = {m: ml.model_from_crn(W.config(m, n_traj=1).crn) for m in (0, 1, 2, 3)}
+    params = ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32, form=ml.ML_FORM_PERSISTENT,
+                                  max_steps=MAX_STEPS, jacobian=ml.ML_JAC_ANALYTIC)
+    total_traj = sum(q["workload"].n_traj for q in reqs)
+
+    # one request per launch, in arrival order: measured service times, queueing by the
+    # arrival process (f_i = max(a_i, f_{i-1}) + s_i)
+    for m in models:  # warm the per-model tables and kernels
+        w1 = W.config(m, n_traj=64)
+        ml.ml_simulate_host(models[m], 64, w1.x0, w1.T[:64] if w1.T.size > 1 else w1.T,
+                            None if w1.theta is None else w1.theta[:64], params=params)
+    service = []
+    for q in reqs:
+        wl = q["workload"]
+        t0 = time.perf_counter()
+        ml.ml_simulate_host(models[q["model_index"]], wl.n_traj, wl.x0, wl.T, wl.theta,
+                            params=params, seed=wl.seed, traj_id_base=wl.traj_id_base)
+        service.append(time.perf_counter() - t0)
+    arr = np.array([q["arrival_s"] for q in reqs])
+    fin = np.zeros(len(reqs))
+    prev = 0.0
+    for i, (a, sv) in enumerate(zip(arr, service)):
+        prev = max(a, prev) + sv
+        fin[i] = prev
+    lat_seq = fin - arr
+    seq = {"p50_latency_ms": 1e3 * float(np.percentile(lat_seq, 50)),
+           "p99_latency_ms": 1e3 * float(np.percentile(lat_seq, 99)),
+           "sustained_traj_per_s": total_traj / (fin[-1] - arr[0]),
+           "busy_s": float(sum(service))}
+
+    # continuous batching: open-loop arrivals submitted by a thread at their times
+    srv = ml.ml_server(budget, max_inflight, params)
+    handles = [None] * len(reqs)
+
+    def submitter(t_start):
+        for i, q in enumerate(reqs):
+            dt = t_start + q["arrival_s"] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            wl = q["workload"]
+            handles[i] = srv.submit(models[q["model_index"]], wl.n_traj, wl.x0, wl.T, wl.theta,
+                                    seed=wl.seed, traj_id_base=wl.traj_id_base)
+
+    t_start = time.perf_counter()
+    th = threading.Thread(target=submitter, args=(t_start,))
+    th.start()
+    th.join()
+    lat = []
+    for h in handles:
+        h.wait(-1)
+        lat.append(h.result()["latency_s"])
+    t_end = time.perf_counter()
+    st = srv.stats()
+    # the completion of the last request, measured from the first arrival
+    makespan = max(t_end - t_start - reqs[0]["arrival_s"], 1e-9)
+    for h in handles:
+        h.free()
+    srv.close()
+    lat = np.array(lat)
+    return {"requests": len(reqs), "arrival_rate_hz": rate_hz, "window_s": seconds,
+            "trajectories": int(total_traj),
+            "models": "immigration-death, dimerisation, gene expression, random 50x100 (horizons scaled, see workloads.SERVING_HORIZON_SCALE)",
+            "p50_latency_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_latency_ms": 1e3 * float(np.percentile(lat, 99)),
+            "sustained_traj_per_s": total_traj / makespan,
+            "peak_inflight": st["peak_inflight"], "max_inflight": max_inflight,
+            "peak_device_bytes": st["peak_bytes"], "budget_bytes": budget,
+            "one_request_per_launch": seq}
 
 
 # ---------------------------------------------------------------------------------
@@ -372,6 +453,8 @@ def run_ours(args):
         rows = stats_util.compare(g, oout, g_res=stats_util.G_RESOLUTION_FAST)
         line["parity"] = {"fast_vs_oracle": stats_util.summary(rows), "n_compared": n,
                           "bad_status": res_fast["bad_status"]}
+    if rank == 0 and world == 1 and args.serving_seconds > 0 and not args.ncu:
+        line["serving"] = run_serving(ml, args.serving_seconds)
     if rank == 0:
         print(json.dumps(line, default=float), flush=True)
     if world > 1:

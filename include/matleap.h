@@ -209,6 +209,62 @@ int ml_simulate_noalloc(const ml_model* model, int64_t n_traj, const double* the
                         uint64_t traj_id_base, int64_t* X_out, int64_t* r_out, double* G_out,
                         uint32_t* status_out, int64_t* counters_out, void* cuda_stream);
 
+/* Number of species N / reactions M of the model (>= 1), or ML_ERR_ARG. */
+int ml_model_num_species(const ml_model* model);
+int ml_model_num_reactions(const ml_model* model);
+
+/* ---- continuous-batching server --------------------------------------------------- *
+ * Serves simulate requests of different models and sizes as they arrive (paper Section
+ * 2: the simulator is called repeatedly with new parameter matrices, e.g. inside a
+ * particle filter).  A scheduler thread admits requests in arrival order whenever one of
+ * max_inflight slots and enough of the device-memory budget are free, keeps each
+ * admitted request's inputs and outputs in a device arena of hbm_budget_bytes, runs it on
+ * the slot's own stream (admitted requests execute concurrently on the GPU) and copies the
+ * results to pinned host memory.  Results depend only on the request (random numbers are
+ * keyed by trajectory id), never on what else is in flight. */
+typedef struct ml_server ml_server;
+typedef struct ml_request ml_request;
+
+/* Creates a server on the current device.  hbm_budget_bytes >= 1 MiB is reserved at once;
+ * 1 <= max_inflight <= 64; p = simulation parameters for every request (NULL = defaults;
+ * use_graph is ignored).  Errors: ML_ERR_ARG, ML_ERR_OOM, ML_ERR_CUDA (no device). */
+int ml_server_create(size_t hbm_budget_bytes, int32_t max_inflight, const ml_sim_params* p,
+                     ml_server** out);
+
+/* Queues a request without blocking: host inputs in the layouts of ml_simulate (theta
+ * [n][M] or NULL, x0 [N] or [n][N], T [1] or [n]) are copied at once, so the caller may
+ * reuse its buffers on return.  *out is owned by the caller (ml_request_free).
+ * Errors: ML_ERR_ARG; ML_ERR_BUSY if the request alone exceeds the budget or the server
+ * is shutting down; ML_ERR_OOM. */
+int ml_server_submit(ml_server* server, const ml_model* model, int64_t n_traj,
+                     const double* theta, const int64_t* x0, int32_t x0_per_traj,
+                     const double* T, int32_t T_per_traj, uint64_t seed,
+                     uint64_t traj_id_base, ml_request** out);
+
+/* Waits up to timeout_ms (< 0: no limit) for the request.  ML_OK when its results are
+ * ready, ML_ERR_TIMEOUT if it is still queued or running, else the request's error. */
+int ml_request_wait(ml_server* server, ml_request* req, int32_t timeout_ms);
+
+/* Copies a finished request's results to host buffers (any may be NULL): X [n][N],
+ * r [n][M], G [n][M], status [n], counters [n][4]; latency_s = completion - submission,
+ * queue_s = admission - submission.  ML_ERR_BUSY if not finished. */
+int ml_request_result(const ml_request* req, int64_t* X_out, int64_t* r_out, double* G_out,
+                      uint32_t* status_out, int64_t* counters_out, double* latency_s,
+                      double* queue_s);
+
+/* Frees a finished request (ML_ERR_BUSY while it is queued or running).  Free requests
+ * before destroying their server (or pass server = NULL afterwards). */
+int ml_request_free(ml_server* server, ml_request* req);
+
+/* Counters since creation: requests admitted and completed, trajectories admitted, peak
+ * arena bytes in use, peak number of requests in flight (any pointer may be NULL). */
+int ml_server_stats(ml_server* server, int64_t* admitted, int64_t* completed,
+                    int64_t* trajectories, size_t* peak_bytes, int32_t* peak_inflight);
+
+/* Stops admitting, fails requests that were never admitted (ML_ERR_BUSY), waits for the
+ * running ones and frees the server.  NULL is a no-op. */
+int ml_server_destroy(ml_server* server);
+
 /* Number of kernel launches the last ml_simulate/ml_simulate_host call on this model
  * issued (a graph replay counts its kernel nodes), or ML_ERR_ARG. */
 int64_t ml_model_last_launch_count(const ml_model* model);

@@ -40,6 +40,7 @@ def _units():
                   [f"-DML_FAST={fast}"] + ([] if fast else ["-fmad=false"])))
     u.append(("api.cu", "api.o", []))
     u.append(("noalloc.cu", "noalloc.o", []))
+    u.append(("server.cu", "server.o", []))
     return u
 
 

@@ -691,6 +691,16 @@ int ml_model_destroy(ml_model* m) {
   return ML_OK;
 }
 
+int ml_model_num_species(const ml_model* m) {
+  if (!m) return fail(ML_ERR_ARG, "model is NULL");
+  return m->N;
+}
+
+int ml_model_num_reactions(const ml_model* m) {
+  if (!m) return fail(ML_ERR_ARG, "model is NULL");
+  return m->M;
+}
+
 int ml_model_num_pairs(const ml_model* m) {
   if (!m) return fail(ML_ERR_ARG, "model is NULL");
   return m->n_pairs;

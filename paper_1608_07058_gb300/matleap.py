@@ -72,6 +72,17 @@ def lib():
         L.ml_simulate.argtypes = sim
         L.ml_simulate_host.argtypes = sim
         L.ml_simulate_noalloc.argtypes = sim
+        L.ml_model_num_species.argtypes = [v]
+        L.ml_model_num_reactions.argtypes = [v]
+        L.ml_server_create.argtypes = [C.c_size_t, C.c_int32, P(ml_sim_params), P(v)]
+        L.ml_server_submit.argtypes = [v, v, C.c_int64, v, v, C.c_int32, v, C.c_int32,
+                                       C.c_uint64, C.c_uint64, P(v)]
+        L.ml_request_wait.argtypes = [v, v, C.c_int32]
+        L.ml_request_result.argtypes = [v, v, v, v, v, v, P(C.c_double), P(C.c_double)]
+        L.ml_request_free.argtypes = [v, v]
+        L.ml_server_stats.argtypes = [v, P(C.c_int64), P(C.c_int64), P(C.c_int64),
+                                      P(C.c_size_t), P(C.c_int32)]
+        L.ml_server_destroy.argtypes = [v]
         L.ml_autotune.argtypes = [v, C.c_int64, v, v, C.c_int32, v, C.c_int32,
                                   P(ml_sim_params), C.c_uint64, C.c_int64, P(ml_sim_params), v]
         _lib = L
@@ -244,3 +255,85 @@ def ml_autotune(model: Model, n_traj: int, x0, T, theta=None,
 def model_from_crn(crn) -> Model:
     """Convenience: an ml_model from a workloads.CRN."""
     return ml_model_create(crn.orders, crn.stoich, crn.rates)
+
+
+# ---- continuous-batching server -----------------------------------------------------
+
+class ml_request:
+    """A submitted request (owns the C handle)."""
+
+    def __init__(self, server, handle, model, n):
+        self.server, self.handle, self.model, self.n = server, handle, model, n
+
+    def wait(self, timeout_ms: int = -1) -> bool:
+        """True when finished; False on timeout; raises on a failed request."""
+        rc = lib().ml_request_wait(C.c_void_p(self.server.handle), C.c_void_p(self.handle),
+                                   timeout_ms)
+        if rc == ML_ERR_TIMEOUT:
+            return False
+        _check(rc)
+        return True
+
+    def result(self) -> dict:
+        N, M, n = self.model.N, self.model.M, self.n
+        out = {"X": np.empty((n, N), np.int64), "r": np.empty((n, M), np.int64),
+               "G": np.empty((n, M), np.float64), "status": np.empty(n, np.uint32),
+               "counters": np.empty((n, 4), np.int64)}
+        lat, q = C.c_double(), C.c_double()
+        _check(lib().ml_request_result(C.c_void_p(self.handle), *[C.c_void_p(out[k].ctypes.data)
+                                       for k in ("X", "r", "G", "status", "counters")],
+                                       C.byref(lat), C.byref(q)))
+        out["latency_s"], out["queue_s"] = lat.value, q.value
+        return out
+
+    def free(self):
+        if self.handle:
+            _check(lib().ml_request_free(C.c_void_p(self.server.handle) if self.server.handle else None,
+                                         C.c_void_p(self.handle)))
+            self.handle = None
+
+
+class ml_server:
+    """Continuous-batching server (ml_server_* entry points)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 8,
+                 params: Optional[ml_sim_params] = None):
+        h = C.c_void_p()
+        p = params if params is not None else ml_default_params()
+        _check(lib().ml_server_create(hbm_budget_bytes, max_inflight, C.byref(p), C.byref(h)))
+        self.handle = h.value
+
+    def submit(self, model: Model, n_traj: int, x0, T, theta=None, seed: int = 0,
+               traj_id_base: int = 0) -> ml_request:
+        x0a = np.ascontiguousarray(x0, np.int64)
+        Ta = np.ascontiguousarray(np.atleast_1d(T), np.float64)
+        tha = None if theta is None else np.ascontiguousarray(theta, np.float64)
+        h = C.c_void_p()
+        _check(lib().ml_server_submit(C.c_void_p(self.handle), C.c_void_p(model.handle), n_traj,
+                                      None if tha is None else C.c_void_p(tha.ctypes.data),
+                                      C.c_void_p(x0a.ctypes.data), int(x0a.ndim == 2),
+                                      C.c_void_p(Ta.ctypes.data), int(Ta.size > 1), seed,
+                                      traj_id_base, C.byref(h)))
+        return ml_request(self, h.value, model, n_traj)
+
+    def stats(self) -> dict:
+        a, c, t = C.c_int64(), C.c_int64(), C.c_int64()
+        pb, pi = C.c_size_t(), C.c_int32()
+        _check(lib().ml_server_stats(C.c_void_p(self.handle), C.byref(a), C.byref(c), C.byref(t),
+                                     C.byref(pb), C.byref(pi)))
+        return {"admitted": a.value, "completed": c.value, "trajectories": t.value,
+                "peak_bytes": pb.value, "peak_inflight": pi.value}
+
+    def close(self):
+        if self.handle:
+            lib().ml_server_destroy(C.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+ml_server_create = ml_server

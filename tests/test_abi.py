@@ -115,3 +115,12 @@ def test_trajectory_id_range(ml):
     with pytest.raises(ml.MatleapError) as e:
         ml.ml_simulate(m, 10, x0, T, traj_id_base=2**32 - 5)
     assert e.value.code == ml.ML_ERR_ARG
+
+
+def test_server_without_device_fails_cleanly(ml):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    with pytest.raises(ml.MatleapError) as e:
+        ml.ml_server(16 << 20, 2)
+    assert e.value.code in (ml.ML_ERR_CUDA, ml.ML_ERR_OOM)
