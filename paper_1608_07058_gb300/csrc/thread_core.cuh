@@ -55,6 +55,49 @@ __device__ __forceinline__ T comb_factor_deriv(T v, int m) {
   return ((T(3) * (v * v) - T(6) * v) + T(2)) / T(6);
 }
 
+// Double-float (hi + lo FP32 pair) arithmetic for the fast-precision reaction pick: sums
+// by TwoSum (Knuth) renormalized with Fast2Sum, about 46 significant bits, all on the
+// FP32 pipe.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_norm(float s, float e) {
+  const float hi = s + e;
+  return DF{hi, e - (hi - s)};
+}
+__device__ __forceinline__ DF df_add(DF a, float b) {
+  const float s = a.hi + b;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (b - bb);
+  return df_norm(s, err + a.lo);
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (b.hi - bb);
+  return df_norm(s, err + (a.lo + b.lo));
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.hi, -b.lo}); }
+__device__ __forceinline__ bool df_lt(DF a, DF b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+// u * t for a 48-bit uniform u = (w_hi>>8) 2^-24 + ((w_lo>>8) + 1/2) 2^-48 in (0, 1).
+__device__ __forceinline__ DF df_uniform_times(DF t, uint32_t w_hi, uint32_t w_lo) {
+  const float uh = (float)(w_hi >> 8) * 0x1p-24f;
+  const float ul = ((float)(w_lo >> 8) + 0.5f) * 0x1p-48f;
+  const float p = uh * t.hi;
+  const float e = fmaf(uh, t.hi, -p);
+  return df_norm(p, e + (uh * t.lo + ul * t.hi));
+}
+
+// Compensated (Kahan) FP32 accumulation: the sum is s - c.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 // Highest-order-reaction factor h_s (Cao 2006) from the species' flags and count.
 template <class R>
 __device__ __forceinline__ R hor_factor(uint8_t f, long long x) {
@@ -421,9 +464,9 @@ struct ThreadTraj {
   // Inverse-CDF pick of a reaction with probability v_j / sum v, from the second uniform
   // of block w (words 2, 3).  Reference: sequential prefix sums in index order (the
   // canonical order), target u * sum with the lane-tree sum.  Fast: the same search over
-  // FP64 prefix sums of the FP32 values with a 52-bit uniform, so reactions far below the
-  // total (propensities spanning many decades) keep their exact share.  Rounding that
-  // leaves no hit picks the last positive entry.
+  // double-float prefix sums of the FP32 values with a 48-bit uniform, so reactions far
+  // below the total (propensities spanning many decades) keep their exact share without
+  // FP64 work.  Rounding that leaves no hit picks the last positive entry.
   __device__ static __forceinline__ int pick_reaction(const R (&v)[MM], const Words4& w) {
     int pk = -1, last = -1;
     if (P::kRef) {
@@ -436,16 +479,16 @@ struct ThreadTraj {
         if (pk < 0 && target < acc) pk = j;
       }
     } else {
-      double tot = 0.0;
+      DF tot{0.f, 0.f};
 #pragma unroll
-      for (int j = 0; j < MM; ++j) tot += (double)v[j];
-      const double target = u01_f64(w.w2, w.w3) * tot;
-      double acc = 0.0;
+      for (int j = 0; j < MM; ++j) tot = df_add(tot, (float)v[j]);
+      const DF target = df_uniform_times(tot, w.w2, w.w3);
+      DF acc{0.f, 0.f};
 #pragma unroll
       for (int j = 0; j < MM; ++j) {
         if (v[j] > R(0)) last = j;
-        acc += (double)v[j];
-        if (pk < 0 && target < acc) pk = j;
+        acc = df_add(acc, (float)v[j]);
+        if (pk < 0 && df_lt(target, acc)) pk = j;
       }
     }
     return pk < 0 ? last : pk;
@@ -496,7 +539,59 @@ struct ThreadTraj {
 
     // SSA burst (Gillespie 1977 direct method): at most n_max firings at outer step
     // `step`; g, a, a0 are current on entry.
+    // Fast precision: inside a burst G_j and the elapsed time are accumulated in
+    // compensated FP32 and folded into the FP64 totals once at the end of the burst.
+    auto ssa_burst_fast = [&](int n_max, R a0) {
+      const double rem = T - t;
+      const float remf = (float)rem;
+      float el = 0.f, elc = 0.f;
+      float Gs[MM], Gc[MM];
+#pragma unroll
+      for (int j = 0; j < MM; ++j) Gs[j] = Gc[j] = 0.f;
+      bool to_horizon = false;
+      for (int b = 0; b < n_max; ++b) {
+        if (b > 0) {
+          eval_props(md, x, th, g, a);
+          a0 = lane_tree_sum<MM, R>(a);
+        }
+        if (a0 == R(0)) {
+          to_horizon = true;
+          break;
+        }
+        const Words4 w = philox_block(k0, k1, id, step, Mr + 2u, (uint32_t)b);
+        const float dt = (float)(-P::log(P::u(w, 0)) / a0);
+        if ((el - elc) + dt > remf) {
+          to_horizon = true;
+          break;
+        }
+#pragma unroll
+        for (int j = 0; j < MM; ++j) kahan_add(Gs[j], Gc[j], (float)g[j] * dt);
+        kahan_add(el, elc, dt);
+        const int pick = pick_reaction(a, w);
+#pragma unroll
+        for (int s = 0; s < NM; ++s) x[s] += md.nu[pick][s];
+#pragma unroll
+        for (int j = 0; j < MM; ++j) r[j] += (j == pick) ? 1 : 0;
+        cnt[2] += 1;
+      }
+      const double elapsed = (double)el - (double)elc;
+#pragma unroll
+      for (int j = 0; j < MM; ++j) G[j] = G[j] + ((double)Gs[j] - (double)Gc[j]);
+      if (to_horizon) {
+        const double left = rem - elapsed > 0.0 ? rem - elapsed : 0.0;
+#pragma unroll
+        for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)g[j] * left;
+        t = T;
+      } else {
+        t = t + elapsed;
+      }
+    };
+
     auto ssa_burst = [&](int n_max, R a0) {
+      if (!P::kRef) {
+        ssa_burst_fast(n_max, a0);
+        return;
+      }
       for (int b = 0; b < n_max; ++b) {
         if (b > 0) {
           eval_props(md, x, th, g, a);

@@ -155,10 +155,11 @@ struct WarpTraj {
 
   // Inverse-CDF pick of a reaction with probability v_j / sum v (v in shared memory,
   // owned values in vl) from the second uniform of block w.  Reference: sequential prefix
-  // in index order with target u * (lane-tree sum), the canonical order.  Fast: FP64
-  // prefix sums of the FP32 values over lane-major order with a 52-bit uniform, so
-  // reactions many decades below the total keep their exact share.  Rounding that leaves
-  // no hit picks the last positive entry.  All lanes return the same index.
+  // in index order with target u * (lane-tree sum), the canonical order.  Fast: double-
+  // float prefix sums of the FP32 values over lane-major order with a 48-bit uniform, so
+  // reactions many decades below the total keep their exact share without FP64 work.
+  // Rounding that leaves no hit picks the last positive entry.  All lanes return the
+  // same index.
   __device__ static int pick(const R* v, const R (&vl)[kRPL], const Words4& w, int M,
                              int lane) {
     if (P::kRef) {
@@ -176,34 +177,37 @@ struct WarpTraj {
       }
       return pk < 0 ? last : pk;
     } else {
-      double S = 0.0;
+      DF S{0.f, 0.f};
 #pragma unroll
       for (int q = 0; q < kRPL; ++q)
-        if (lane + 32 * q < M) S += (double)vl[q];
-      double E = S;  // inclusive scan over lanes
+        if (lane + 32 * q < M) S = df_add(S, (float)vl[q]);
+      DF E = S;  // inclusive scan over lanes
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
-        const double o = __shfl_up_sync(0xffffffffu, E, d);
-        if (lane >= d) E += o;
+        const DF o{__shfl_up_sync(0xffffffffu, E.hi, d), __shfl_up_sync(0xffffffffu, E.lo, d)};
+        if (lane >= d) E = df_add(E, o);
       }
-      const double target = u01_f64(w.w2, w.w3) * __shfl_sync(0xffffffffu, E, 31);
-      const unsigned hit = __ballot_sync(0xffffffffu, target < E && S > 0.0);
+      const DF tot{__shfl_sync(0xffffffffu, E.hi, 31), __shfl_sync(0xffffffffu, E.lo, 31)};
+      const DF target = df_uniform_times(tot, w.w2, w.w3);
+      DF Ex{__shfl_up_sync(0xffffffffu, E.hi, 1), __shfl_up_sync(0xffffffffu, E.lo, 1)};
+      if (lane == 0) Ex = DF{0.f, 0.f};
+      const unsigned hit = __ballot_sync(0xffffffffu, df_lt(target, E) && S.hi > 0.f);
       int src;
       if (hit) src = __ffs(hit) - 1;
       else {
-        const unsigned pos = __ballot_sync(0xffffffffu, S > 0.0);
+        const unsigned pos = __ballot_sync(0xffffffffu, S.hi > 0.f);
         src = pos ? 31 - __clz(pos) : 0;
       }
       int pk = -1, last = -1;
       if (lane == src) {
-        double acc = E - S;
+        DF acc = Ex;
 #pragma unroll
         for (int q = 0; q < kRPL; ++q) {
           const int j = lane + 32 * q;
           if (j < M && vl[q] > R(0)) {
             last = j;
-            acc += (double)vl[q];
-            if (pk < 0 && target < acc) pk = j;
+            acc = df_add(acc, (float)vl[q]);
+            if (pk < 0 && df_lt(target, acc)) pk = j;
           }
         }
         if (pk < 0) pk = last;
@@ -455,7 +459,63 @@ struct WarpTraj {
       __syncwarp();
     };
 
+    // Fast precision: inside a burst each lane accumulates its G_j and the elapsed time in
+    // compensated FP32 and folds them into the FP64 totals once at the end of the burst.
+    auto ssa_burst_fast = [&](int n_max, R a0) {
+      const double rem = T - t;
+      const float remf = (float)rem;
+      float el = 0.f, elc = 0.f;
+      float Gs[kRPL], Gc[kRPL];
+#pragma unroll
+      for (int q = 0; q < kRPL; ++q) Gs[q] = Gc[q] = 0.f;
+      bool to_horizon = false;
+      for (int b = 0; b < n_max; ++b) {
+        if (b > 0) {
+          eval_props();
+          a0 = tree_sum(a, lane, M);
+        }
+        if (a0 == R(0)) {
+          to_horizon = true;
+          break;
+        }
+        const Words4 w = philox_block(k0, k1, id, step, Mr + 2u, (uint32_t)b);
+        const float dt = (float)(-P::log(P::u(w, 0)) / a0);
+        if ((el - elc) + dt > remf) {
+          to_horizon = true;
+          break;
+        }
+#pragma unroll
+        for (int q = 0; q < kRPL; ++q) kahan_add(Gs[q], Gc[q], (float)g[q] * dt);
+        kahan_add(el, elc, dt);
+        const int pk = pick(a_s, a, w, M, lane);
+        if (pk >= 0) {
+          const int e0 = md.rx_ptr[pk], e1 = md.rx_ptr[pk + 1];
+          for (int e = e0 + lane; e < e1; e += 32) sl.x[md.rx_s[e]] += md.rx_nu[e];
+#pragma unroll
+          for (int q = 0; q < kRPL; ++q)
+            if (lane + 32 * q == pk) r[q] += 1;
+          cnt[2] += 1;
+        }
+        __syncwarp();
+      }
+      const double elapsed = (double)el - (double)elc;
+#pragma unroll
+      for (int q = 0; q < kRPL; ++q) G[q] = G[q] + ((double)Gs[q] - (double)Gc[q]);
+      if (to_horizon) {
+        const double left = rem - elapsed > 0.0 ? rem - elapsed : 0.0;
+#pragma unroll
+        for (int q = 0; q < kRPL; ++q) G[q] = G[q] + (double)g[q] * left;
+        t = T;
+      } else {
+        t = t + elapsed;
+      }
+    };
+
     auto ssa_burst = [&](int n_max, R a0) {
+      if (!P::kRef) {
+        ssa_burst_fast(n_max, a0);
+        return;
+      }
       for (int b = 0; b < n_max; ++b) {
         if (b > 0) {
           eval_props();
