@@ -215,12 +215,17 @@ def run_serving(ml, seconds, rate_hz=200.0, seed=11, max_inflight=8, budget=8 <<
         ml.ml_simulate_host(models[m], 64, w1.x0, w1.T[:64] if w1.T.size > 1 else w1.T,
                             None if w1.theta is None else w1.theta[:64], params=params)
     service = []
+    per_model = {m: {"requests": 0, "trajectories": 0, "busy_s": 0.0} for m in models}
     for q in reqs:
         wl = q["workload"]
         t0 = time.perf_counter()
         ml.ml_simulate_host(models[q["model_index"]], wl.n_traj, wl.x0, wl.T, wl.theta,
                             params=params, seed=wl.seed, traj_id_base=wl.traj_id_base)
         service.append(time.perf_counter() - t0)
+        pm = per_model[q["model_index"]]
+        pm["requests"] += 1
+        pm["trajectories"] += wl.n_traj
+        pm["busy_s"] += service[-1]
     arr = np.array([q["arrival_s"] for q in reqs])
     fin = np.zeros(len(reqs))
     prev = 0.0
@@ -231,7 +236,10 @@ def run_serving(ml, seconds, rate_hz=200.0, seed=11, max_inflight=8, budget=8 <<
     seq = {"p50_latency_ms": 1e3 * float(np.percentile(lat_seq, 50)),
            "p99_latency_ms": 1e3 * float(np.percentile(lat_seq, 99)),
            "sustained_traj_per_s": total_traj / (fin[-1] - arr[0]),
-           "busy_s": float(sum(service))}
+           "saturated_traj_per_s": total_traj / float(sum(service)),
+           "busy_s": float(sum(service)),
+           "per_model": {W.config(m, n_traj=1).name: {**v, "traj_per_s": v["trajectories"] / max(v["busy_s"], 1e-9)}
+                         for m, v in per_model.items()}}
 
     # continuous batching: open-loop arrivals submitted by a thread at their times
     srv = ml.ml_server(budget, max_inflight, params)
@@ -260,6 +268,16 @@ def run_serving(ml, seconds, rate_hz=200.0, seed=11, max_inflight=8, budget=8 <<
     makespan = max(t_end - t_start - reqs[0]["arrival_s"], 1e-9)
     for h in handles:
         h.free()
+    # capacity: every request submitted at once, time to drain
+    t0 = time.perf_counter()
+    hs = [srv.submit(models[q["model_index"]], q["workload"].n_traj, q["workload"].x0,
+                     q["workload"].T, q["workload"].theta, seed=q["workload"].seed,
+                     traj_id_base=q["workload"].traj_id_base) for q in reqs]
+    for h in hs:
+        h.wait(-1)
+    drain = time.perf_counter() - t0
+    for h in hs:
+        h.free()
     srv.close()
     lat = np.array(lat)
     return {"requests": len(reqs), "arrival_rate_hz": rate_hz, "window_s": seconds,
@@ -268,6 +286,8 @@ def run_serving(ml, seconds, rate_hz=200.0, seed=11, max_inflight=8, budget=8 <<
             "p50_latency_ms": 1e3 * float(np.percentile(lat, 50)),
             "p99_latency_ms": 1e3 * float(np.percentile(lat, 99)),
             "sustained_traj_per_s": total_traj / makespan,
+            "saturated_traj_per_s": total_traj / drain,
+            "saturated_vs_one_request_per_launch": (total_traj / drain) / (total_traj / sum(service)),
             "peak_inflight": st["peak_inflight"], "max_inflight": max_inflight,
             "peak_device_bytes": st["peak_bytes"], "budget_bytes": budget,
             "one_request_per_launch": seq}
