@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--jacobian", choices=["fd", "analytic"], default="analytic",
                     help="Jacobian of the implicit solve, same for both forms")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the default launch shape (for very long workloads)")
     ap.add_argument("--serving-seconds", type=float, default=4.0,
                     help="arrival window of the serving mix (0 = skip it)")
     ap.add_argument("--ncu", action="store_true",
@@ -341,7 +343,7 @@ def run_ours(args):
     jac = ml.ML_JAC_ANALYTIC if args.jacobian == "analytic" else ml.ML_JAC_FD
     fast = ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32, form=ml.ML_FORM_PERSISTENT,
                                 use_graph=1, max_steps=MAX_STEPS, jacobian=jac)
-    if not args.ncu:
+    if not args.ncu and not args.no_autotune:
         best = ml.ml_autotune(model, B, x0, T, theta, params=fast, n_sample=min(B, 32768))
         fast.shape, fast.block_size, fast.ctas_per_sm = best.shape, best.block_size, best.ctas_per_sm
     plain = ml.ml_default_params(precision=ml.ML_PREC_REF_FP64, form=ml.ML_FORM_PLAIN,
@@ -400,8 +402,9 @@ def run_ours(args):
             "config": {"workload": workload_name(w), "form": "persistent refill kernel, CUDA graph, autotuned",
                        "precision": "FP32 propensities/tau/Poisson, FP64 t/G/Newton",
                        "jacobian": args.jacobian,
-                       "shape": {"shape": {ml.ML_SHAPE_THREAD: "thread", ml.ML_SHAPE_WARP: "warp",
-                                           ml.ML_SHAPE_THREAD_OCC: "thread (128-register build)"}.get(fast.shape, "auto"),
+                       "shape": {"shape": {ml.ML_SHAPE_THREAD: "thread, round-based", ml.ML_SHAPE_WARP: "warp",
+                                           ml.ML_SHAPE_THREAD_OCC: "thread, round-based, occupancy build",
+                                           ml.ML_SHAPE_THREAD_SEQ: "thread, sequential per lane"}.get(fast.shape, "auto"),
                                  "block_size": fast.block_size, "ctas_per_sm": fast.ctas_per_sm},
                        "l2": "flushed between steps (256 MB write)"},
             "leap_steps_per_s": leap_steps / (ms_fast / 1e3),

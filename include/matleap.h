@@ -77,10 +77,15 @@ extern "C" {
 
 /* ---- kernel shapes ---------------------------------------------------------------- */
 #define ML_SHAPE_AUTO 0   /* thread per trajectory when the model fits, else warp     */
-#define ML_SHAPE_THREAD 1 /* one trajectory per thread (N <= 8, M <= 16)               */
+#define ML_SHAPE_THREAD 1 /* one trajectory per thread (N <= 8, M <= 16), round-based  */
 #define ML_SHAPE_WARP 2   /* one trajectory per warp (N <= 64, M <= 128)               */
 #define ML_SHAPE_THREAD_OCC 3 /* fast precision only: one trajectory per thread, built
-                                 for 128 registers (twice the resident warps, spills) */
+                                 for more resident warps (about 168 registers, some
+                                 spilling, at most 128 threads per CTA)              */
+#define ML_SHAPE_THREAD_SEQ 4 /* one trajectory per thread, each run to its end before
+                                 the next (whole SSA bursts at once); the default
+                                 thread shape interleaves leap evaluations and slices
+                                 of SSA bursts round by round                         */
 
 /* ---- Jacobian of the implicit solve (Section 1: estimated numerically, or the
  *      symbolic Jacobian of Section 3) ------------------------------------------------- */

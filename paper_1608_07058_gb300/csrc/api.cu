@@ -199,6 +199,23 @@ bool warp_fits(const ml_model& m) {
   return m.N <= mlk::kWarpMaxN && m.M <= mlk::kWarpMaxM && nnz <= (size_t)mlk::kWarpMaxM * 8;
 }
 
+mlk::KernelEntry thread_seq_entry(int precision, int variant) {
+  if (precision == ML_PREC_FAST_FP32) {
+    switch (variant) {
+      case 0: return mlk::thread_seq_entry_fast_0();
+      case 1: return mlk::thread_seq_entry_fast_1();
+      case 2: return mlk::thread_seq_entry_fast_2();
+      default: return mlk::thread_seq_entry_fast_3();
+    }
+  }
+  switch (variant) {
+    case 0: return mlk::thread_seq_entry_ref_0();
+    case 1: return mlk::thread_seq_entry_ref_1();
+    case 2: return mlk::thread_seq_entry_ref_2();
+    default: return mlk::thread_seq_entry_ref_3();
+  }
+}
+
 mlk::KernelEntry thread_entry(int precision, int variant, bool occ = false) {
   if (precision == ML_PREC_FAST_FP32 && occ) {
     switch (variant) {
@@ -257,7 +274,7 @@ int check_params(const ml_sim_params& p) {
     return fail(ML_ERR_ARG, "unknown precision %d", p.precision);
   if (p.form != ML_FORM_PLAIN && p.form != ML_FORM_PERSISTENT)
     return fail(ML_ERR_ARG, "unknown form %d", p.form);
-  if (p.shape < ML_SHAPE_AUTO || p.shape > ML_SHAPE_THREAD_OCC)
+  if (p.shape < ML_SHAPE_AUTO || p.shape > ML_SHAPE_THREAD_SEQ)
     return fail(ML_ERR_ARG, "unknown shape %d", p.shape);
   if (p.shape == ML_SHAPE_THREAD_OCC && p.precision != ML_PREC_FAST_FP32)
     return fail(ML_ERR_ARG, "the 128-register thread build exists in fast precision only");
@@ -317,6 +334,7 @@ int ensure_tables(ml_model* m, DeviceState& st, int shape, int variant) {
 
 struct Plan {
   bool occ = false;
+  bool seq = false;
   int shape = ML_SHAPE_THREAD;
   int variant = 0;
   mlk::KernelEntry entry{};
@@ -338,29 +356,35 @@ int make_plan(ml_model* m, DeviceState& st, const ml_sim_params& p, int64_t n_tr
                                   : (variant >= 0 ? ML_SHAPE_THREAD : ML_SHAPE_WARP);
   }
   const bool occ = shape == ML_SHAPE_THREAD_OCC;
+  const bool seq = shape == ML_SHAPE_THREAD_SEQ;
   if (occ && p.precision != ML_PREC_FAST_FP32) shape = ML_SHAPE_THREAD;  // tuned for fast only
-  if (shape == ML_SHAPE_THREAD_OCC) shape = ML_SHAPE_THREAD;
+  if (shape == ML_SHAPE_THREAD_OCC || shape == ML_SHAPE_THREAD_SEQ) shape = ML_SHAPE_THREAD;
   if (shape == ML_SHAPE_THREAD && variant < 0)
     return fail(ML_ERR_UNSUPPORTED, "model %dx%d is too large for one thread per trajectory",
                 m->N, m->M);
   if (shape == ML_SHAPE_WARP && !warp_fits(*m))
     return fail(ML_ERR_UNSUPPORTED, "model %dx%d is too large for the warp kernel", m->N, m->M);
-  const mlk::KernelEntry entry = shape == ML_SHAPE_THREAD
-                                     ? thread_entry(p.precision, variant, occ && p.precision == ML_PREC_FAST_FP32)
-                                     : warp_entry(p.precision);
+  const mlk::KernelEntry entry =
+      shape == ML_SHAPE_THREAD
+          ? (seq ? thread_seq_entry(p.precision, variant)
+                 : thread_entry(p.precision, variant, occ && p.precision == ML_PREC_FAST_FP32))
+          : warp_entry(p.precision);
   if (!entry.kernel || !entry.launch)
     return fail(ML_ERR_UNSUPPORTED, "no kernel built for this shape and precision");
   int rc = ensure_tables(m, st, shape, variant);
   if (rc != ML_OK) return rc;
   plan->shape = shape;
   plan->occ = occ && p.precision == ML_PREC_FAST_FP32;
+  plan->seq = seq;
   plan->variant = variant;
   plan->entry = entry;
   plan->tables = shape == ML_SHAPE_THREAD ? st.thread_tables[variant] : st.warp_tables;
-  const bool tuned_here = tuned && (tuned->shape == shape || (occ && tuned->shape == ML_SHAPE_THREAD_OCC));
+  const bool tuned_here = tuned && (tuned->shape == shape || (occ && tuned->shape == ML_SHAPE_THREAD_OCC) ||
+                                    (seq && tuned->shape == ML_SHAPE_THREAD_SEQ));
   int block = p.block_size ? p.block_size
                            : (tuned_here && tuned->block ? tuned->block
                                                          : (shape == ML_SHAPE_THREAD ? 128 : 128));
+  if (plan->occ && block > 128) block = 128;  // the occupancy build is bounded to 128 threads
   const int per_cta = shape == ML_SHAPE_THREAD ? block : block / 32;  // trajectories
   plan->smem = shape == ML_SHAPE_WARP ? mlk::warp_smem_bytes(block / 32, m->N, m->M, p.precision) : 0;
   if (plan->smem > 48 * 1024) {
@@ -433,7 +457,7 @@ void fill_args(const ml_model* m, const ml_sim_params& p, int64_t n_traj, const 
 // updated in place when they change.
 int launch_graph(DeviceState& st, const ml_sim_params& p, const Plan& plan,
                  mlk::SimArgs& a, cudaStream_t stream) {
-  const int key2 = plan.shape == ML_SHAPE_THREAD ? plan.variant + (plan.occ ? 50 : 0) : 100;
+  const int key2 = plan.shape == ML_SHAPE_THREAD ? plan.variant + (plan.occ ? 50 : 0) + (plan.seq ? 25 : 0) : 100;
   GraphCache& gc = st.graphs[{p.precision, key2}];
   const void* tables = plan.tables;
   void* kargs[2] = {const_cast<void**>(&tables), &a};
@@ -863,13 +887,14 @@ int ml_autotune(ml_model* m, int64_t n_traj, const double* theta, const int64_t*
   const int thread_ok = thread_variant_for(*m) >= 0;
   const int warp_ok = warp_fits(*m);
   std::vector<ml_sim_params> cands;
-  for (int shape = ML_SHAPE_THREAD; shape <= ML_SHAPE_THREAD_OCC; ++shape) {
-    const bool thread_like = shape == ML_SHAPE_THREAD || shape == ML_SHAPE_THREAD_OCC;
+  for (int shape = ML_SHAPE_THREAD; shape <= ML_SHAPE_THREAD_SEQ; ++shape) {
+    const bool thread_like = shape != ML_SHAPE_WARP;
     if ((thread_like && !thread_ok) || (shape == ML_SHAPE_WARP && !warp_ok)) continue;
     if (shape == ML_SHAPE_THREAD_OCC && p.precision != ML_PREC_FAST_FP32) continue;
     if (p.shape != ML_SHAPE_AUTO && p.shape != shape) continue;
     const int blocks[] = {64, 128, 256};
     for (int b : blocks) {
+      if (shape == ML_SHAPE_THREAD_OCC && b > 128) continue;
       const int per_sm_opts[] = {0, 1, 2, 4, 8};
       for (int per_sm : per_sm_opts) {
         if (p.form != ML_FORM_PERSISTENT && per_sm != 0) continue;

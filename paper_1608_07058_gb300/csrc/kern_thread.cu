@@ -1,8 +1,9 @@
 // One thread-per-trajectory kernel variant, selected at compile time:
 //   ML_FAST = 0: reference precision (compile with -fmad=false), 1: fast precision;
 //   ML_VARIANT: index into the (species, reactions) capacity table;
-//   ML_THREAD_MIN_BLOCKS = 2 (fast only): the 128-register build (more resident warps,
-//   some spilling), offered to the autotuner as a separate shape.
+//   ML_THREAD_MIN_BLOCKS = 2 (fast only): the occupancy build (at most 128 threads per
+//   CTA, about 168 registers, more resident warps, some spilling), offered to the
+//   autotuner as a separate shape.
 #include "thread_core.cuh"
 
 #ifndef ML_VARIANT
@@ -32,9 +33,20 @@ cudaError_t launch(const void* dm, const SimArgs& a, int grid, int block, size_t
       static_cast<const ThreadModel<kNM, kMM>*>(dm), a);
   return cudaGetLastError();
 }
+cudaError_t launch_seq(const void* dm, const SimArgs& a, int grid, int block, size_t smem,
+                       cudaStream_t s) {
+  k_thread_seq<kNM, kMM, Prec><<<grid, block, smem, s>>>(
+      static_cast<const ThreadModel<kNM, kMM>*>(dm), a);
+  return cudaGetLastError();
+}
 }  // namespace
 
 KernelEntry ML_CAT(thread_entry_, ML_PNAME, ML_VARIANT)() {
   return KernelEntry{&launch, reinterpret_cast<const void*>(&k_thread<kNM, kMM, Prec>)};
 }
+#if ML_THREAD_MIN_BLOCKS != 2
+KernelEntry ML_CAT(thread_seq_entry_, ML_PNAME, ML_VARIANT)() {
+  return KernelEntry{&launch_seq, reinterpret_cast<const void*>(&k_thread_seq<kNM, kMM, Prec>)};
+}
+#endif
 }  // namespace mlk

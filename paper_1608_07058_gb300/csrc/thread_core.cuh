@@ -179,10 +179,14 @@ constexpr int kPtrsMaxTrials = 256;
 
 // PTRS: Hoermann (1993), transformed rejection with squeeze, for mean mu >= 10.  Trial b
 // uses block b of the stream: U from the first uniform, V from the second.
+struct PoissonDraw {
+  long long k;
+  uint32_t flags;  // ML_ST_PTRS_CAP when the trial cap was hit
+};
+
 template <class P>
-__device__ __noinline__ long long poisson_ptrs(typename P::R mu, uint32_t k0, uint32_t k1,
-                                               uint32_t id, uint32_t step, uint32_t stream,
-                                               uint32_t& status) {
+__device__ __noinline__ PoissonDraw poisson_ptrs(typename P::R mu, uint32_t k0, uint32_t k1,
+                                                 uint32_t id, uint32_t step, uint32_t stream) {
   using R = typename P::R;
   const R slam = P::sqrt(mu);
   const R loglam = P::log(mu);
@@ -196,7 +200,7 @@ __device__ __noinline__ long long poisson_ptrs(typename P::R mu, uint32_t k0, ui
     const R V = P::u(w, 1);
     const R us = R(0.5) - fabs(U);
     const R kd = floor((((R(2) * a) / us + b) * U + mu) + R(0.43));
-    if (us >= R(0.07) && V <= v_r) return (long long)kd;
+    if (us >= R(0.07) && V <= v_r) return PoissonDraw{(long long)kd, 0u};
     if (kd < R(0) || (us < R(0.013) && V > us)) continue;
     const R lhs = (P::log(V) + P::log(inv_alpha)) - P::log(a / (us * us) + b);
     R rhs;
@@ -211,10 +215,9 @@ __device__ __noinline__ long long poisson_ptrs(typename P::R mu, uint32_t k0, ui
       rhs = ((z - mu) + (z - R(1)) * P::log1p((mu - z) * iz)) - R(0.5) * P::log(z) -
             R(0.91893853320467274178) - iz * (R(1) / R(12) - (iz * iz) * (R(1) / R(360)));
     }
-    if (lhs <= rhs) return (long long)kd;
+    if (lhs <= rhs) return PoissonDraw{(long long)kd, 0u};
   }
-  status |= ML_ST_PTRS_CAP;
-  return (long long)floor(mu + R(0.5));
+  return PoissonDraw{(long long)floor(mu + R(0.5)), ML_ST_PTRS_CAP};
 }
 
 // Poisson(mu): 0 for mu <= 0 (no draw); inversion by sequential search below 10; PTRS.
@@ -238,10 +241,11 @@ __device__ __forceinline__ long long poisson_draw(typename P::R mu, uint32_t k0,
     }
     return k;
   }
-  if (!P::kRef && mu > R(4.0e6)) {
-    return poisson_ptrs<PrecWide>((double)mu, k0, k1, id, step, stream, status);
-  }
-  return poisson_ptrs<P>(mu, k0, k1, id, step, stream, status);
+  const PoissonDraw d = (!P::kRef && mu > R(4.0e6))
+                            ? poisson_ptrs<PrecWide>((double)mu, k0, k1, id, step, stream)
+                            : poisson_ptrs<P>(mu, k0, k1, id, step, stream);
+  status |= d.flags;
+  return d.k;
 }
 
 template <int NM, int MM, class P>
@@ -335,7 +339,7 @@ struct ThreadTraj {
   // working precision R (FP64 in reference precision; FP32 in fast precision, where an
   // approximate Jacobian changes only the rate of convergence, not the FP64 root).
   // Returns 0 converged, 1 not converged, 2 singular.
-  __device__ static int implicit_solve(const Model& md, const R (&th)[MM],
+  __device__ static __forceinline__ int implicit_solve(const Model& md, const R (&th)[MM],
                                        const long long (&x)[NM], uint32_t nc,
                                        const long long (&Pk)[MM], const R (&a)[MM],
                                        double tau, double tol, int maxit, double fd_h,
@@ -494,86 +498,167 @@ struct ThreadTraj {
     return pk < 0 ? last : pk;
   }
 
-  // The whole trajectory.
-  __device__ static void run(const Model& md, const SimArgs& A, long long i) {
-    const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
-    const uint32_t id = (uint32_t)(A.id_base + (unsigned long long)i);
-    const uint32_t Mr = (uint32_t)A.M;  // stream numbering uses the real M
-    uint32_t status = 0;
+};
 
-    R th[MM];
+
+// One trajectory per thread, driven as a per-lane state machine so that a warp does not
+// hold lanes in one phase while others run a long phase: in each round a lane performs
+// either one leap evaluation (propensities, critical set, step sizes, leap or burst
+// decision) or a bounded slice of its SSA burst.  Finished lanes refill from the work
+// queue inside the loop (persistent form).  Each lane performs exactly the arithmetic of
+// the sequential algorithm, so results do not depend on the schedule.
+template <int NM, int MM, class P>
+struct ThreadLane {
+  using R = typename P::R;
+  using TT = ThreadTraj<NM, MM, P>;
+  using Model = ThreadModel<NM, MM>;
+  enum : int { kIdle = 0, kEval = 1, kSsa = 2, kDone = 3 };
+
+  long long i;
+  uint32_t id, status, step;
+  int reject_run, mode;
+  double t, T;
+  R th[MM];
+  long long x[NM];
+  long long r[MM];
+  double G[MM];
+  long long cnt[4];
+  R g[MM], a[MM];
+  // SSA burst
+  int b, n_max;
+  R a0;
+
+  __device__ __forceinline__ void start(const Model& md, const SimArgs& A, long long idx) {
+    i = idx;
+    id = (uint32_t)(A.id_base + (unsigned long long)idx);
+    status = 0;
     bool bad = false;
 #pragma unroll
     for (int j = 0; j < MM; ++j) {
       double v = 0.0;
-      if (j < A.M) v = A.theta ? A.theta[i * A.M + j] : md.rates[j];
+      if (j < A.M) v = A.theta ? A.theta[idx * A.M + j] : md.rates[j];
       if (!(v >= 0.0)) bad = true;
       th[j] = (R)v;
     }
-    long long x[NM];
-    const int64_t* x0 = A.x0_per ? A.x0 + i * A.N : A.x0;
+    const int64_t* x0 = A.x0_per ? A.x0 + idx * A.N : A.x0;
 #pragma unroll
     for (int s = 0; s < NM; ++s) {
       x[s] = s < A.N ? x0[s] : 0;
       if (x[s] < 0) bad = true;
     }
-    const double T = A.T_per ? A.T[i] : A.T[0];
-    long long r[MM];
-    double G[MM];
+    T = A.T_per ? A.T[idx] : A.T[0];
 #pragma unroll
     for (int j = 0; j < MM; ++j) {
       r[j] = 0;
       G[j] = 0.0;
     }
-    long long cnt[4] = {0, 0, 0, 0};
-    double t = 0.0;
-    uint32_t step = 0;
-    int reject_run = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cnt[c] = 0;
+    t = 0.0;
+    step = 0;
+    reject_run = 0;
     if (bad) {
       status |= ML_ST_BAD_INPUT;
       t = T;
     }
-    if (T != T) t = 0.0;  // NaN horizon: the loop below never runs
+    if (T != T) t = 0.0;  // NaN horizon: finishes at once
+    mode = kEval;
+  }
 
-    R g[MM], a[MM];
-
-    // SSA burst (Gillespie 1977 direct method): at most n_max firings at outer step
-    // `step`; g, a, a0 are current on entry.
-    // Fast precision: inside a burst G_j and the elapsed time are accumulated in
-    // compensated FP32 and folded into the FP64 totals once at the end of the burst.
-    auto ssa_burst_fast = [&](int n_max, R a0) {
-      const double rem = T - t;
-      const float remf = (float)rem;
-      float el = 0.f, elc = 0.f;
-      float Gs[MM], Gc[MM];
+  __device__ __forceinline__ void finish(const SimArgs& A, bool staged) {
 #pragma unroll
-      for (int j = 0; j < MM; ++j) Gs[j] = Gc[j] = 0.f;
-      bool to_horizon = false;
-      for (int b = 0; b < n_max; ++b) {
-        if (b > 0) {
-          eval_props(md, x, th, g, a);
-          a0 = lane_tree_sum<MM, R>(a);
-        }
-        if (a0 == R(0)) {
-          to_horizon = true;
+    for (int s = 0; s < NM; ++s)
+      if (s < A.N) A.X[i * A.N + s] = x[s];
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      if (j < A.M) {
+        A.r[i * A.M + j] = r[j];
+        A.G[i * A.M + j] = G[j];
+      }
+    }
+    A.status[i] = status | (staged ? 0u : ML_ST_STAGE_TIMEOUT);
+    if (A.counters) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) A.counters[i * 4 + c] = cnt[c];
+    }
+    mode = kIdle;
+  }
+
+  __device__ __forceinline__ void begin_burst(int n) {
+    mode = kSsa;
+    b = 0;
+    n_max = n;
+  }
+
+  __device__ __forceinline__ void end_burst() {
+    step++;
+    reject_run = 0;
+    mode = kEval;
+  }
+
+  // Up to n_slice firings of the SSA burst (Gillespie 1977 direct method) at outer step
+  // `step`, firing index b; g, a, a0 are current for b == 0.  Fast precision accumulates
+  // the slice's G increments and elapsed time in compensated FP32 and folds them into
+  // the FP64 totals at the end of the slice.
+  __device__ __forceinline__ void ssa_slice(const Model& md, const SimArgs& A, int n_slice) {
+    const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
+    const uint32_t Mr = (uint32_t)A.M;
+    const double rem = T - t;
+    const float remf = (float)rem;
+    float el = 0.f, elc = 0.f;
+    float Gs[MM], Gc[MM];
+#pragma unroll
+    for (int j = 0; j < MM; ++j) Gs[j] = Gc[j] = 0.f;
+    bool to_horizon = false, burst_over = false;
+    for (int k = 0; k < n_slice; ++k) {
+      if (b > 0) {
+        TT::eval_props(md, x, th, g, a);
+        a0 = lane_tree_sum<MM, R>(a);
+      }
+      if (a0 == R(0)) {
+        to_horizon = burst_over = true;
+        break;
+      }
+      const Words4 w = philox_block(k0, k1, id, step, Mr + 2u, (uint32_t)b);
+      if (P::kRef) {
+        const R dt = -P::log(P::u(w, 0)) / a0;
+        const double tn = t + (double)dt;
+        if (tn > T) {
+          to_horizon = burst_over = true;
           break;
         }
-        const Words4 w = philox_block(k0, k1, id, step, Mr + 2u, (uint32_t)b);
+#pragma unroll
+        for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)g[j] * (double)dt;
+        t = tn;
+      } else {
         const float dt = (float)(-P::log(P::u(w, 0)) / a0);
         if ((el - elc) + dt > remf) {
-          to_horizon = true;
+          to_horizon = burst_over = true;
           break;
         }
 #pragma unroll
         for (int j = 0; j < MM; ++j) kahan_add(Gs[j], Gc[j], (float)g[j] * dt);
         kahan_add(el, elc, dt);
-        const int pick = pick_reaction(a, w);
-#pragma unroll
-        for (int s = 0; s < NM; ++s) x[s] += md.nu[pick][s];
-#pragma unroll
-        for (int j = 0; j < MM; ++j) r[j] += (j == pick) ? 1 : 0;
-        cnt[2] += 1;
       }
+      const int pick = TT::pick_reaction(a, w);
+#pragma unroll
+      for (int s = 0; s < NM; ++s) x[s] += md.nu[pick][s];
+#pragma unroll
+      for (int j = 0; j < MM; ++j) r[j] += (j == pick) ? 1 : 0;
+      cnt[2] += 1;
+      if (++b >= n_max) {
+        burst_over = true;
+        break;
+      }
+    }
+    if (P::kRef) {
+      if (to_horizon) {
+        const double rm = T - t;
+#pragma unroll
+        for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)g[j] * rm;
+        t = T;
+      }
+    } else {
       const double elapsed = (double)el - (double)elc;
 #pragma unroll
       for (int j = 0; j < MM; ++j) G[j] = G[j] + ((double)Gs[j] - (double)Gc[j]);
@@ -585,70 +670,39 @@ struct ThreadTraj {
       } else {
         t = t + elapsed;
       }
-    };
+    }
+    if (burst_over) end_burst();
+  }
 
-    auto ssa_burst = [&](int n_max, R a0) {
-      if (!P::kRef) {
-        ssa_burst_fast(n_max, a0);
-        return;
-      }
-      for (int b = 0; b < n_max; ++b) {
-        if (b > 0) {
-          eval_props(md, x, th, g, a);
-          a0 = lane_tree_sum<MM, R>(a);
-        }
-        if (a0 == R(0)) {
-          const double rem = T - t;
+  // One outer step: either a committed leap (stays in kEval), the start of an SSA burst,
+  // or the end of the trajectory.
+  __device__ __forceinline__ void eval_phase(const Model& md, const SimArgs& A) {
+    const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
+    const uint32_t Mr = (uint32_t)A.M;  // stream numbering uses the real M
+    if (!(t < T)) {
+      mode = kDone;
+      return;
+    }
+    if ((long long)step >= A.max_steps) {
+      status |= ML_ST_STEP_LIMIT;
+      mode = kDone;
+      return;
+    }
+    TT::eval_props(md, x, th, g, a);
+    a0 = lane_tree_sum<MM, R>(a);
+    if (a0 == R(0)) {
+      const double rm = T - t;
 #pragma unroll
-          for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)g[j] * rem;
-          t = T;
-          return;
-        }
-        const Words4 w = philox_block(k0, k1, id, step, Mr + 2u, (uint32_t)b);
-        const R u1 = P::u(w, 0);
-        const R dt = -P::log(u1) / a0;
-        const double tn = t + (double)dt;
-        if (tn > T) {
-          const double rem = T - t;
-#pragma unroll
-          for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)g[j] * rem;
-          t = T;
-          return;
-        }
-#pragma unroll
-        for (int j = 0; j < MM; ++j) {
-          if (P::kRef) G[j] = G[j] + (double)g[j] * (double)dt;
-          else G[j] = G[j] + (double)(g[j] * dt);  // FP32 increment, FP64 accumulation
-        }
-        t = tn;
-        const int pick = pick_reaction(a, w);
-#pragma unroll
-        for (int s = 0; s < NM; ++s) x[s] += md.nu[pick][s];
-#pragma unroll
-        for (int j = 0; j < MM; ++j) r[j] += (j == pick) ? 1 : 0;
-        cnt[2] += 1;
-      }
-    };
-
+      for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)g[j] * rm;
+      t = T;
+      mode = kDone;
+      return;
+    }
+    int burst = 0;
     const R eps = (R)A.eps;
-    for (;;) {
-      if (!(t < T)) break;
-      if ((long long)step >= A.max_steps) {
-        status |= ML_ST_STEP_LIMIT;
-        break;
-      }
-      eval_props(md, x, th, g, a);
-      const R a0 = lane_tree_sum<MM, R>(a);
-      if (a0 == R(0)) {
-        const double rem = T - t;
-#pragma unroll
-        for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)g[j] * rem;
-        t = T;
-        break;
-      }
-      int burst = 0;  // > 0: run an SSA burst of this many firings after the attempts
-      if (A.mode == ML_MODE_SSA_ONLY) burst = A.n_ssa_ex;
-      else {
+    if (A.mode == ML_MODE_SSA_ONLY) {
+      burst = A.n_ssa_ex;
+    } else {
       // critical reactions
       uint32_t nc = 0;
       R ac[MM];
@@ -671,7 +725,7 @@ struct ThreadTraj {
         ac[j] = crit ? a[j] : R(0);
       }
       const R a0c = lane_tree_sum<MM, R>(ac);
-      const R tau_ex = tau_select(md, a, x, nc, eps);
+      const R tau_ex = TT::tau_select(md, a, x, nc, eps);
       // partial equilibrium and the implicit step size
       bool implicit = false;
       R tau1 = tau_ex;
@@ -690,14 +744,14 @@ struct ThreadTraj {
           }
         }
         if (pe != 0) {
-          const R tau_im = tau_select(md, a, x, nc & ~pe, eps);
+          const R tau_im = TT::tau_select(md, a, x, nc & ~pe, eps);
           if (tau_im > (R)A.stiff_ratio * tau_ex) {
             implicit = true;
             tau1 = tau_im;
           }
         }
       }
-      // attempt loop
+      // attempt loop: tau2, SSA switch, leap, negativity check
       for (;;) {
         if (reject_run >= A.max_reject) {
           status |= ML_ST_REJECT_LIMIT;
@@ -714,21 +768,21 @@ struct ThreadTraj {
           burst = implicit ? A.n_ssa_im : A.n_ssa_ex;
           break;
         }
-        const double rem = T - t;
+        const double rm = T - t;
         R tau = tau1;
         if (tau2 < tau) tau = tau2;
         bool at_horizon = false;
-        if ((R)rem <= tau) {
-          tau = (R)rem;
+        if ((R)rm <= tau) {
+          tau = (R)rm;
           at_horizon = true;
         }
-        const bool crit_fire = (tau2 <= tau1) && (tau2 <= (R)rem);
+        const bool crit_fire = (tau2 <= tau1) && (tau2 <= (R)rm);
         long long K[MM];
 #pragma unroll
         for (int j = 0; j < MM; ++j) K[j] = 0;
         if (crit_fire) {
           const Words4 w = philox_block(k0, k1, id, step, Mr + 1u, 0u);
-          const int pick = pick_reaction(ac, Words4{0u, 0u, w.w0, w.w1});
+          const int pick = TT::pick_reaction(ac, Words4{0u, 0u, w.w0, w.w1});
 #pragma unroll
           for (int j = 0; j < MM; ++j) K[j] = (j == pick) ? 1 : 0;
         }
@@ -742,8 +796,9 @@ struct ThreadTraj {
         if (implicit_step) {
           double y[NM];
           const double taud = (double)tau;
-          const int rc = implicit_solve(md, th, x, nc, K, a, taud, A.newton_tol,
-                                        A.newton_maxit, A.fd_h, A.jacobian == ML_JAC_ANALYTIC, y);
+          const int rc = TT::implicit_solve(md, th, x, nc, K, a, taud, A.newton_tol,
+                                            A.newton_maxit, A.fd_h,
+                                            A.jacobian == ML_JAC_ANALYTIC, y);
           if (rc != 0) {
             status |= ML_ST_NEWTON_FAIL;
             implicit = false;
@@ -754,7 +809,7 @@ struct ThreadTraj {
 #pragma unroll
           for (int j = 0; j < MM; ++j) {
             if ((nc >> j) & 1u) {
-              const double ayj = (double)th[j] * g_real(md, j, y);
+              const double ayj = (double)th[j] * TT::g_real(md, j, y);
               const double v = (ayj * taud + (double)K[j]) - (double)a[j] * taud;
               const double rv = round(v);
               K[j] = rv > 0.0 ? (long long)rv : 0;
@@ -782,7 +837,7 @@ struct ThreadTraj {
         const R half_r = tau * R(0.5);
 #pragma unroll
         for (int j = 0; j < MM; ++j) {
-          const R gn = g_int(md, j, xn);
+          const R gn = TT::g_int(md, j, xn);
           r[j] += K[j];
           if (P::kRef) G[j] = G[j] + half * ((double)g[j] + (double)gn);
           else G[j] = G[j] + (double)(half_r * (g[j] + gn));  // FP32 increment
@@ -795,52 +850,80 @@ struct ThreadTraj {
         reject_run = 0;
         break;
       }
-      }
-      if (burst > 0) {
-        ssa_burst(burst, a0);
-        step++;
-        reject_run = 0;
-      }
     }
-
-    // write-back
-#pragma unroll
-    for (int s = 0; s < NM; ++s)
-      if (s < A.N) A.X[i * A.N + s] = x[s];
-#pragma unroll
-    for (int j = 0; j < MM; ++j) {
-      if (j < A.M) {
-        A.r[i * A.M + j] = r[j];
-        A.G[i * A.M + j] = G[j];
-      }
-    }
-    A.status[i] = status;
-    if (A.counters) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) A.counters[i * 4 + c] = cnt[c];
-    }
+    if (burst > 0) begin_burst(burst);
   }
 };
 
 #ifndef ML_THREAD_MIN_BLOCKS
-#define ML_THREAD_MIN_BLOCKS 1  // 2: a 128-register build with twice the resident warps
+#define ML_THREAD_MIN_BLOCKS 1
+#endif
+#if ML_THREAD_MIN_BLOCKS == 2
+// the occupancy build: at most 128 threads per CTA, about 168 registers, 3 CTAs per SM
+#define ML_THREAD_BOUNDS __launch_bounds__(128, 3)
+#else
+#define ML_THREAD_BOUNDS __launch_bounds__(256, 1)
 #endif
 
-// Kernel: stage the model tables once per CTA, then simulate.  Plain form (queue null):
-// thread i runs trajectory i.  Persistent form: each thread claims trajectory indices
-// from the device queue until none is left, so a thread that finishes early
-// immediately refills its slot.
+// Warp schedule: in every round a lane that needs a leap evaluation performs one, and a
+// lane inside an SSA burst performs up to kSsaPerRound firings (about the cost of one
+// evaluation), so lanes in different phases progress together instead of a whole burst
+// holding the warp.
+constexpr int kSsaPerRound = 8;
+
+// Kernel: stage the model tables once per CTA, then run the lane state machine.  Plain
+// form (queue null): thread i runs trajectory i.  Persistent form: lanes claim trajectory
+// indices from the device queue and refill as soon as their trajectory ends.
 template <int NM, int MM, class P>
-__global__ void __launch_bounds__(256, ML_THREAD_MIN_BLOCKS) k_thread(const ThreadModel<NM, MM>* __restrict__ gmd,
-                                                const SimArgs args) {
+__global__ void ML_THREAD_BOUNDS k_thread(const ThreadModel<NM, MM>* __restrict__ gmd,
+                                          const SimArgs args) {
   __shared__ ThreadModel<NM, MM> smd;
   __shared__ uint64_t mbar;
   const bool staged = stage_model_bulk(&smd, gmd, (uint32_t)thread_model_bytes<NM, MM>(), &mbar);
+  using Lane = ThreadLane<NM, MM, P>;
+  Lane L;
+  L.mode = Lane::kIdle;
+  const long long first = args.queue ? (long long)atomicAdd(args.queue, 1ULL)
+                                     : (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (first < args.n_traj) L.start(smd, args, first);
+  for (;;) {
+    if (L.mode == Lane::kDone) {
+      L.finish(args, staged);
+      if (args.queue) {
+        const long long nxt = (long long)atomicAdd(args.queue, 1ULL);
+        if (nxt < args.n_traj) L.start(smd, args, nxt);
+      }
+    }
+    if (!__any_sync(0xffffffffu, L.mode != Lane::kIdle)) break;
+    if (L.mode == Lane::kEval) {
+      L.eval_phase(smd, args);
+    } else if (L.mode == Lane::kSsa) {
+      L.ssa_slice(smd, args, kSsaPerRound);
+    }
+  }
+}
+
+// Sequential per-lane driver over the same lane state machine: each thread runs its
+// trajectory to the end (whole SSA bursts at once) before claiming the next one.  It has
+// less scheduling overhead and suits leap-dominated workloads; the autotuner picks between
+// the two drivers.
+template <int NM, int MM, class P>
+__global__ void ML_THREAD_BOUNDS k_thread_seq(const ThreadModel<NM, MM>* __restrict__ gmd,
+                                              const SimArgs args) {
+  __shared__ ThreadModel<NM, MM> smd;
+  __shared__ uint64_t mbar;
+  const bool staged = stage_model_bulk(&smd, gmd, (uint32_t)thread_model_bytes<NM, MM>(), &mbar);
+  using Lane = ThreadLane<NM, MM, P>;
+  Lane L;
   long long i = args.queue ? (long long)atomicAdd(args.queue, 1ULL)
                            : (long long)blockIdx.x * blockDim.x + threadIdx.x;
   while (i < args.n_traj) {
-    ThreadTraj<NM, MM, P>::run(smd, args, i);
-    if (!staged) args.status[i] |= ML_ST_STAGE_TIMEOUT;
+    L.start(smd, args, i);
+    while (L.mode != Lane::kDone) {
+      if (L.mode == Lane::kEval) L.eval_phase(smd, args);
+      else L.ssa_slice(smd, args, 0x7fffffff);
+    }
+    L.finish(args, staged);
     if (!args.queue) break;
     i = (long long)atomicAdd(args.queue, 1ULL);
   }

@@ -205,7 +205,8 @@ def test_autotune_picks_a_valid_shape(ml):
                           params=ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32,
                                                       form=ml.ML_FORM_PERSISTENT),
                           n_sample=8192)
-    assert best.shape in (ml.ML_SHAPE_THREAD, ml.ML_SHAPE_WARP)
+    assert best.shape in (ml.ML_SHAPE_THREAD, ml.ML_SHAPE_WARP, ml.ML_SHAPE_THREAD_OCC,
+                          ml.ML_SHAPE_THREAD_SEQ)
     assert best.block_size in (64, 128, 256)
 
 
@@ -312,3 +313,15 @@ def test_fast_poisson_sampler_law(ml, oracle, mu):
         p = np.diff(np.concatenate([[0.0], stats.poisson.cdf(edges[1:-1] - 1, mu), [1.0]]))
         keep = p * n > 5
         assert stats.chisquare(obs[keep], p[keep] * n * obs[keep].sum() / (p[keep] * n).sum()).pvalue > 1e-4
+
+
+@pytest.mark.parametrize("shape", [1, 4])
+@pytest.mark.parametrize("cfg,n", [(1, 3000), (2, 500)])
+def test_ref_bit_parity_thread_drivers(ml, oracle, shape, cfg, n):
+    """Both thread drivers (round-based and sequential per lane) in both launch forms run
+    the same per-lane arithmetic: bit-identical to the oracle."""
+    w = W.config(cfg, n_traj=n)
+    o = run_oracle(oracle, w.crn, n, w.x0, w.T, w.theta, seed=41)
+    for form in (0, 1):
+        g = run_gpu(ml, w.crn, n, w.x0, w.T, w.theta, seed=41, shape=shape, form=form)
+        assert_bit_parity(g, o, f"shape{shape} form{form}")
