@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default launch shape (for very long workloads)")
+    ap.add_argument("--shape", type=int, default=0,
+                    help="force a launch shape (ML_SHAPE_*; skips the autotuner)")
+    ap.add_argument("--block", type=int, default=0, help="force threads per CTA")
     ap.add_argument("--serving-seconds", type=float, default=4.0,
                     help="arrival window of the serving mix (0 = skip it)")
     ap.add_argument("--ncu", action="store_true",
@@ -343,11 +346,16 @@ def run_ours(args):
     jac = ml.ML_JAC_ANALYTIC if args.jacobian == "analytic" else ml.ML_JAC_FD
     fast = ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32, form=ml.ML_FORM_PERSISTENT,
                                 use_graph=1, max_steps=MAX_STEPS, jacobian=jac)
-    if not args.ncu and not args.no_autotune:
+    if args.shape:
+        fast.shape, fast.block_size = args.shape, args.block
+    elif not args.ncu and not args.no_autotune:
         best = ml.ml_autotune(model, B, x0, T, theta, params=fast, n_sample=min(B, 32768))
         fast.shape, fast.block_size, fast.ctas_per_sm = best.shape, best.block_size, best.ctas_per_sm
+    # the plain form: one launch, each thread runs its trajectory to the end, FP64
     plain = ml.ml_default_params(precision=ml.ML_PREC_REF_FP64, form=ml.ML_FORM_PLAIN,
-                                 max_steps=MAX_STEPS, block_size=128, jacobian=jac)
+                                 max_steps=MAX_STEPS, block_size=128, jacobian=jac,
+                                 shape=ml.ML_SHAPE_THREAD_SEQ if W.config(args.config, n_traj=1).crn.n_reactions <= 16
+                                 else ml.ML_SHAPE_WARP)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
 
     def timed(params, seed0):
@@ -404,7 +412,8 @@ def run_ours(args):
                        "jacobian": args.jacobian,
                        "shape": {"shape": {ml.ML_SHAPE_THREAD: "thread, round-based", ml.ML_SHAPE_WARP: "warp",
                                            ml.ML_SHAPE_THREAD_OCC: "thread, round-based, occupancy build",
-                                           ml.ML_SHAPE_THREAD_SEQ: "thread, sequential per lane"}.get(fast.shape, "auto"),
+                                           ml.ML_SHAPE_THREAD_SEQ: "thread, sequential per lane",
+                                           ml.ML_SHAPE_THREAD_SEQ_OCC: "thread, sequential per lane, occupancy build"}.get(fast.shape, "auto"),
                                  "block_size": fast.block_size, "ctas_per_sm": fast.ctas_per_sm},
                        "l2": "flushed between steps (256 MB write)"},
             "leap_steps_per_s": leap_steps / (ms_fast / 1e3),
@@ -417,7 +426,7 @@ def run_ours(args):
         line["plain_fp64"] = {"value": world * B / (ms_plain / 1e3), "unit": "trajectories/s",
                               "ms_per_step": ms_plain,
                               "leap_steps_per_s": float(counts_plain[:3].sum()) / (ms_plain / 1e3),
-                              "form": "one launch, one thread per trajectory, FP64 reference precision"}
+                              "form": "one launch, one thread per trajectory run to its end, FP64 reference precision"}
         line["batched_vs_plain"] = line["value"] / line["plain_fp64"]["value"]
         line["gpu_launches_plain"] = int(res_plain["launches"])
 

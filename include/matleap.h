@@ -86,6 +86,8 @@ extern "C" {
                                  the next (whole SSA bursts at once); the default
                                  thread shape interleaves leap evaluations and slices
                                  of SSA bursts round by round                         */
+#define ML_SHAPE_THREAD_SEQ_OCC 5 /* fast precision only: the sequential per-lane driver
+                                     in the occupancy build                           */
 
 /* ---- Jacobian of the implicit solve (Section 1: estimated numerically, or the
  *      symbolic Jacobian of Section 3) ------------------------------------------------- */

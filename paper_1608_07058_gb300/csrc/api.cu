@@ -199,7 +199,15 @@ bool warp_fits(const ml_model& m) {
   return m.N <= mlk::kWarpMaxN && m.M <= mlk::kWarpMaxM && nnz <= (size_t)mlk::kWarpMaxM * 8;
 }
 
-mlk::KernelEntry thread_seq_entry(int precision, int variant) {
+mlk::KernelEntry thread_seq_entry(int precision, int variant, bool occ = false) {
+  if (precision == ML_PREC_FAST_FP32 && occ) {
+    switch (variant) {
+      case 0: return mlk::thread_seq_entry_fastocc_0();
+      case 1: return mlk::thread_seq_entry_fastocc_1();
+      case 2: return mlk::thread_seq_entry_fastocc_2();
+      default: return mlk::thread_seq_entry_fastocc_3();
+    }
+  }
   if (precision == ML_PREC_FAST_FP32) {
     switch (variant) {
       case 0: return mlk::thread_seq_entry_fast_0();
@@ -274,9 +282,10 @@ int check_params(const ml_sim_params& p) {
     return fail(ML_ERR_ARG, "unknown precision %d", p.precision);
   if (p.form != ML_FORM_PLAIN && p.form != ML_FORM_PERSISTENT)
     return fail(ML_ERR_ARG, "unknown form %d", p.form);
-  if (p.shape < ML_SHAPE_AUTO || p.shape > ML_SHAPE_THREAD_SEQ)
+  if (p.shape < ML_SHAPE_AUTO || p.shape > ML_SHAPE_THREAD_SEQ_OCC)
     return fail(ML_ERR_ARG, "unknown shape %d", p.shape);
-  if (p.shape == ML_SHAPE_THREAD_OCC && p.precision != ML_PREC_FAST_FP32)
+  if ((p.shape == ML_SHAPE_THREAD_OCC || p.shape == ML_SHAPE_THREAD_SEQ_OCC) &&
+      p.precision != ML_PREC_FAST_FP32)
     return fail(ML_ERR_ARG, "the 128-register thread build exists in fast precision only");
   if (p.block_size != 0 && (p.block_size < 32 || p.block_size > 256 || p.block_size % 32))
     return fail(ML_ERR_ARG, "block_size must be 0 or a multiple of 32 in [32, 256]");
@@ -355,10 +364,11 @@ int make_plan(ml_model* m, DeviceState& st, const ml_sim_params& p, int64_t n_tr
     shape = tuned && tuned->shape ? tuned->shape
                                   : (variant >= 0 ? ML_SHAPE_THREAD : ML_SHAPE_WARP);
   }
-  const bool occ = shape == ML_SHAPE_THREAD_OCC;
-  const bool seq = shape == ML_SHAPE_THREAD_SEQ;
-  if (occ && p.precision != ML_PREC_FAST_FP32) shape = ML_SHAPE_THREAD;  // tuned for fast only
-  if (shape == ML_SHAPE_THREAD_OCC || shape == ML_SHAPE_THREAD_SEQ) shape = ML_SHAPE_THREAD;
+  const int req_shape = shape;
+  const bool occ = (shape == ML_SHAPE_THREAD_OCC || shape == ML_SHAPE_THREAD_SEQ_OCC) &&
+                   p.precision == ML_PREC_FAST_FP32;
+  const bool seq = shape == ML_SHAPE_THREAD_SEQ || shape == ML_SHAPE_THREAD_SEQ_OCC;
+  if (shape != ML_SHAPE_WARP) shape = ML_SHAPE_THREAD;
   if (shape == ML_SHAPE_THREAD && variant < 0)
     return fail(ML_ERR_UNSUPPORTED, "model %dx%d is too large for one thread per trajectory",
                 m->N, m->M);
@@ -366,21 +376,20 @@ int make_plan(ml_model* m, DeviceState& st, const ml_sim_params& p, int64_t n_tr
     return fail(ML_ERR_UNSUPPORTED, "model %dx%d is too large for the warp kernel", m->N, m->M);
   const mlk::KernelEntry entry =
       shape == ML_SHAPE_THREAD
-          ? (seq ? thread_seq_entry(p.precision, variant)
-                 : thread_entry(p.precision, variant, occ && p.precision == ML_PREC_FAST_FP32))
+          ? (seq ? thread_seq_entry(p.precision, variant, occ)
+                 : thread_entry(p.precision, variant, occ))
           : warp_entry(p.precision);
   if (!entry.kernel || !entry.launch)
     return fail(ML_ERR_UNSUPPORTED, "no kernel built for this shape and precision");
   int rc = ensure_tables(m, st, shape, variant);
   if (rc != ML_OK) return rc;
   plan->shape = shape;
-  plan->occ = occ && p.precision == ML_PREC_FAST_FP32;
+  plan->occ = occ;
   plan->seq = seq;
   plan->variant = variant;
   plan->entry = entry;
   plan->tables = shape == ML_SHAPE_THREAD ? st.thread_tables[variant] : st.warp_tables;
-  const bool tuned_here = tuned && (tuned->shape == shape || (occ && tuned->shape == ML_SHAPE_THREAD_OCC) ||
-                                    (seq && tuned->shape == ML_SHAPE_THREAD_SEQ));
+  const bool tuned_here = tuned && tuned->shape == req_shape;
   int block = p.block_size ? p.block_size
                            : (tuned_here && tuned->block ? tuned->block
                                                          : (shape == ML_SHAPE_THREAD ? 128 : 128));
@@ -887,14 +896,15 @@ int ml_autotune(ml_model* m, int64_t n_traj, const double* theta, const int64_t*
   const int thread_ok = thread_variant_for(*m) >= 0;
   const int warp_ok = warp_fits(*m);
   std::vector<ml_sim_params> cands;
-  for (int shape = ML_SHAPE_THREAD; shape <= ML_SHAPE_THREAD_SEQ; ++shape) {
+  for (int shape = ML_SHAPE_THREAD; shape <= ML_SHAPE_THREAD_SEQ_OCC; ++shape) {
     const bool thread_like = shape != ML_SHAPE_WARP;
+    const bool occ_shape = shape == ML_SHAPE_THREAD_OCC || shape == ML_SHAPE_THREAD_SEQ_OCC;
     if ((thread_like && !thread_ok) || (shape == ML_SHAPE_WARP && !warp_ok)) continue;
-    if (shape == ML_SHAPE_THREAD_OCC && p.precision != ML_PREC_FAST_FP32) continue;
+    if (occ_shape && p.precision != ML_PREC_FAST_FP32) continue;
     if (p.shape != ML_SHAPE_AUTO && p.shape != shape) continue;
     const int blocks[] = {64, 128, 256};
     for (int b : blocks) {
-      if (shape == ML_SHAPE_THREAD_OCC && b > 128) continue;
+      if (occ_shape && b > 128) continue;
       const int per_sm_opts[] = {0, 1, 2, 4, 8};
       for (int per_sm : per_sm_opts) {
         if (p.form != ML_FORM_PERSISTENT && per_sm != 0) continue;

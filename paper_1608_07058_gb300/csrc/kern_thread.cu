@@ -44,9 +44,7 @@ cudaError_t launch_seq(const void* dm, const SimArgs& a, int grid, int block, si
 KernelEntry ML_CAT(thread_entry_, ML_PNAME, ML_VARIANT)() {
   return KernelEntry{&launch, reinterpret_cast<const void*>(&k_thread<kNM, kMM, Prec>)};
 }
-#if ML_THREAD_MIN_BLOCKS != 2
 KernelEntry ML_CAT(thread_seq_entry_, ML_PNAME, ML_VARIANT)() {
   return KernelEntry{&launch_seq, reinterpret_cast<const void*>(&k_thread_seq<kNM, kMM, Prec>)};
 }
-#endif
 }  // namespace mlk

@@ -137,6 +137,10 @@ KernelEntry thread_seq_entry_fast_0();
 KernelEntry thread_seq_entry_fast_1();
 KernelEntry thread_seq_entry_fast_2();
 KernelEntry thread_seq_entry_fast_3();
+KernelEntry thread_seq_entry_fastocc_0();
+KernelEntry thread_seq_entry_fastocc_1();
+KernelEntry thread_seq_entry_fastocc_2();
+KernelEntry thread_seq_entry_fastocc_3();
 // Warp-per-trajectory kernels (kern_warp.cu, one object per precision).
 KernelEntry warp_entry_ref();
 KernelEntry warp_entry_fast();

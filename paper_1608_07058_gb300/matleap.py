@@ -24,6 +24,7 @@ ML_MODE_ADAPTIVE, ML_MODE_EXPLICIT_ONLY, ML_MODE_SSA_ONLY = 0, 1, 2
 ML_PREC_REF_FP64, ML_PREC_FAST_FP32 = 0, 1
 ML_FORM_PLAIN, ML_FORM_PERSISTENT = 0, 1
 ML_SHAPE_AUTO, ML_SHAPE_THREAD, ML_SHAPE_WARP, ML_SHAPE_THREAD_OCC, ML_SHAPE_THREAD_SEQ = 0, 1, 2, 3, 4
+ML_SHAPE_THREAD_SEQ_OCC = 5
 ML_JAC_FD, ML_JAC_ANALYTIC = 0, 1
 
 

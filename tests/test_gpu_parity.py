@@ -205,8 +205,7 @@ def test_autotune_picks_a_valid_shape(ml):
                           params=ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32,
                                                       form=ml.ML_FORM_PERSISTENT),
                           n_sample=8192)
-    assert best.shape in (ml.ML_SHAPE_THREAD, ml.ML_SHAPE_WARP, ml.ML_SHAPE_THREAD_OCC,
-                          ml.ML_SHAPE_THREAD_SEQ)
+    assert best.shape in (1, 2, 3, 4, 5)
     assert best.block_size in (64, 128, 256)
 
 
