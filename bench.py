@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--n-traj", type=int, default=None)
+    ap.add_argument("--horizon", type=float, default=None,
+                    help="override the workload's horizon T (one value for every trajectory)")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0,
                     help="target CPU seconds for the oracle baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
@@ -335,6 +337,9 @@ def run_ours(args):
         return t.cpu().numpy()
 
     w = W.config(args.config, n_traj=args.n_traj)
+    if args.horizon is not None:
+        import numpy as np
+        w.T = np.array([args.horizon])
     B = w.n_traj
     id_base = rank * B
     model = ml.model_from_crn(w.crn)
