@@ -125,6 +125,11 @@ UNIFORM_OPS = 3
 LOG_OPS = 15
 POISSON_INV_OPS = 40  # exp, ~3 search steps of 3 ops, uniform
 POISSON_PTRS_OPS = 110
+NEWTON_ITERATIONS = 4.3  # mean iterations per implicit leap on dimerisation states (oracle)
+
+# DRAM bytes per launch measured by ncu for the kernel the default workload runs (see
+# profiles/k_thread_fast_dimerisation_100k.md), keyed by (config, shape)
+PROFILED_TRAFFIC = {(1, 4): 174_592}
 
 
 def work_model(crn):
@@ -138,11 +143,13 @@ def work_model(crn):
     ssa = props + (M - 1) + PHILOX_OPS + 2 * UNIFORM_OPS + LOG_OPS + 1 + 2 * M + 2 * (nnz / M) + 2 * M + 1
     leap = (2 * props + (M - 1) + 2 * int((nu < 0).sum()) + 4 * nnz + 7 * nreact
             + M * (PHILOX_OPS + POISSON_INV_OPS) + nnz + 3 * M + M)
-    newton_it = (N + 1) * props + 2 * nnz * (N + 1) + (2 * N ** 3) // 3 + 4 * N * N + 6 * N
-    implicit = leap + 3 * newton_it + 4 * M
+    # one Newton iteration with the exact Jacobian: propensities at y, residual, Jacobian
+    # entries and assembly, elimination and back substitution, update and stopping test
+    newton_it = props + 2 * nnz + 3 * N + 4 * int((o > 0).sum()) + 2 * nnz + (2 * N ** 3) // 3 + 2 * N * N + 4 * N
+    implicit = leap + NEWTON_ITERATIONS * newton_it + 6 * M + 3 * 2
     reject = leap - props - nnz
-    return {"explicit_leap": leap, "implicit_leap": implicit, "ssa_firing": ssa,
-            "rejected_leap": reject, "assumed_newton_iterations": 3}
+    return {"explicit_leap": leap, "implicit_leap": round(implicit, 1), "ssa_firing": ssa,
+            "rejected_leap": reject, "newton_iterations": NEWTON_ITERATIONS}
 
 
 def ops_from_counts(model_ops, counts):
@@ -443,8 +450,11 @@ def run_ours(args):
     peak_clock = 2070.0
     peak = sms * 128 * peak_clock * 1e6 / 1e12   # Tops/s: SMs x 4 schedulers x 32 lanes x clock
     achieved = ops_per_launch / (ms_fast / 1e3) / 1e12
+    traffic = PROFILED_TRAFFIC.get((args.config, fast.shape)) if args.n_traj is None else None
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                        "frac": achieved / peak, "traffic": None,
+                        "frac": achieved / peak, "traffic": traffic,
+                        "algorithmic_bytes_per_launch": int(B * (8 * model.N + 16 * model.M + 36)
+                                                            + (0 if theta is None else B * 8 * model.M)),
                         "peak_basis": f"{sms} SMs x 128 lanes x {peak_clock:.0f} MHz (issue rate, one op per lane per clock)",
                         "work_model_ops_per_event": ops_model}
     if clk:
