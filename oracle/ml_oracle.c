@@ -935,3 +935,106 @@ int mlo_simulate(int32_t N, int32_t M, const int32_t* orders, const int32_t* sto
   model_free(&md);
   return 0;
 }
+
+
+/* ------------------------------------------------------------------------------------
+ * Bayesian step.  The conjugate posterior of each rate constant given one path's
+ * statistics is Gamma(alpha_j + r_j, beta_j + G_j) (Section 1).
+ * ---------------------------------------------------------------------------------- */
+#define GAMMA_MAX_TRIALS 64
+
+double mlo_gamma(double shape, double rate, uint64_t seed, uint32_t traj_id, uint32_t stream,
+                 uint32_t* status) {
+  if (!(shape > 0.0) || !(rate > 0.0)) return NAN;
+  const int boost = shape < 1.0;
+  const double a = boost ? shape + 1.0 : shape;
+  const double d = a - 1.0 / 3.0;
+  const double c = 1.0 / sqrt(9.0 * d);
+  const uint32_t ctr_step = 0x80000000u + stream;
+  for (uint32_t t = 0; t < GAMMA_MAX_TRIALS; ++t) {
+    uint32_t w[4], w2[4];
+    block_words(seed, traj_id, ctr_step, 0u, 2u * t, w);
+    /* Marsaglia polar method: (v1, v2) uniform in the square, accepted inside the disk */
+    const double v1 = 2.0 * mlo_u01_from_words(w[0], w[1]) - 1.0;
+    const double v2 = 2.0 * mlo_u01_from_words(w[2], w[3]) - 1.0;
+    const double s = v1 * v1 + v2 * v2;
+    if (!(s < 1.0) || s == 0.0) continue;
+    const double z = v1 * sqrt((-2.0 * mlo_log(s)) / s);
+    const double base = 1.0 + c * z;
+    if (!(base > 0.0)) continue;
+    const double v = (base * base) * base;
+    block_words(seed, traj_id, ctr_step, 0u, 2u * t + 1u, w2);
+    const double u = mlo_u01_from_words(w2[0], w2[1]);
+    /* accept iff log u < z^2/2 + d - d v + d log v */
+    if (mlo_log(u) < ((0.5 * (z * z) + d) - d * v) + d * mlo_log(v)) {
+      double x = d * v;
+      if (boost) {
+        const double ub = mlo_u01_from_words(w2[2], w2[3]);
+        x = x * mlo_exp(mlo_log(ub) / shape);
+      }
+      return x / rate;
+    }
+  }
+  if (status) *status |= 1u;
+  return shape / rate; /* the mean, after GAMMA_MAX_TRIALS rejections (never observed) */
+}
+
+int mlo_posterior_sample(int64_t n, int32_t M, const double* alpha, int32_t alpha_per_traj,
+                         const double* beta, int32_t beta_per_traj, const int64_t* r,
+                         const double* G, uint64_t seed, uint64_t traj_id_base,
+                         double* theta_out, uint32_t* status_out) {
+  if (n < 0 || M < 1 || !alpha || !beta || !r || !G || !theta_out) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    uint32_t st = 0;
+    const uint32_t id = (uint32_t)(traj_id_base + (uint64_t)i);
+    for (int32_t j = 0; j < M; ++j) {
+      const double al = alpha_per_traj ? alpha[i * M + j] : alpha[j];
+      const double be = beta_per_traj ? beta[i * M + j] : beta[j];
+      theta_out[i * M + j] = mlo_gamma(al + (double)r[i * M + j], be + G[i * M + j], seed, id,
+                                       (uint32_t)j, &st);
+    }
+    if (status_out) status_out[i] = st;
+  }
+  return 0;
+}
+
+int mlo_resample_systematic(int64_t n, const double* logw, uint64_t seed, uint64_t id_base,
+                            int64_t* ancestors) {
+  if (n < 1 || !logw || !ancestors) return -1;
+  double mx = -INFINITY;
+  for (int64_t i = 0; i < n; ++i)
+    if (logw[i] > mx) mx = logw[i]; /* NaN never compares greater: weight 0 */
+  if (mx == -INFINITY || mx == INFINITY) {
+    for (int64_t k = 0; k < n; ++k) ancestors[k] = -1;
+    return -1;
+  }
+  uint64_t* q = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n);
+  unsigned __int128 total = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double wgt = logw[i] == logw[i] ? mlo_exp(logw[i] - mx) : 0.0; /* in [0, 1] */
+    q[i] = (uint64_t)floor(wgt * 1099511627776.0); /* 2^40 */
+    total += q[i];
+  }
+  if (total == 0) {
+    for (int64_t k = 0; k < n; ++k) ancestors[k] = -1;
+    free(q);
+    return -1;
+  }
+  uint32_t w[4];
+  block_words(seed, (uint32_t)id_base, 0xC0000000u, 0u, 0u, w);
+  const double u = mlo_u01_from_words(w[0], w[1]);
+  const unsigned __int128 uQ = (unsigned __int128)floor(u * (double)(uint64_t)total);
+  /* ancestor k: first i whose inclusive prefix exceeds target_k = (k Q + uQ) / n */
+  unsigned __int128 prefix = 0;
+  int64_t i = 0;
+  for (int64_t k = 0; k < n; ++k) {
+    const unsigned __int128 target = ((unsigned __int128)k * total + uQ) / (unsigned __int128)n;
+    while (i < n && prefix + q[i] <= target) {
+      prefix += q[i];
+      ++i;
+    }
+    ancestors[k] = i < n ? i : n - 1;
+  }
+  free(q);
+  return 0;
+}

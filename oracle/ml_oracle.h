@@ -96,6 +96,29 @@ int mlo_implicit_solve(int32_t N, int32_t M, const int32_t* orders, const int32_
                        const double* P, const double* a_x, double tau, const mlo_params* p,
                        double* y_out, int32_t* iters_out);
 
+/* ---- Bayesian step (Section 1: Gamma(alpha + r, beta + G) posterior) ------------- */
+/* Gamma(shape, rate) draw by Marsaglia & Tsang (2000) with normals from the Marsaglia
+ * polar method; shape < 1 by Gamma(shape + 1) U^(1/shape).  Random numbers: counter
+ * (traj_id, 0x80000000 + stream, 0, block), block 2t the polar pair of trial t, block 2t+1
+ * the acceptance uniform (words 0, 1) and the boost uniform (words 2, 3).  Returns NaN
+ * for shape <= 0 or rate <= 0; sets *status bit 1 if the trial cap was hit. */
+double mlo_gamma(double shape, double rate, uint64_t seed, uint32_t traj_id, uint32_t stream,
+                 uint32_t* status);
+/* theta[i][j] ~ Gamma(alpha_j + r[i][j], beta_j + G[i][j]) for n trajectories (alpha,
+ * beta: [M] or [n][M] with *_per_traj), trajectory i with id traj_id_base + i, stream j. */
+int mlo_posterior_sample(int64_t n, int32_t M, const double* alpha, int32_t alpha_per_traj,
+                         const double* beta, int32_t beta_per_traj, const int64_t* r,
+                         const double* G, uint64_t seed, uint64_t traj_id_base,
+                         double* theta_out, uint32_t* status_out);
+/* Systematic resampling of n particles from log-weights: weights w_i = exp(logw_i - max)
+ * are quantized to integers q_i = floor(w_i 2^40) (so every prefix sum is exact), Q = sum
+ * q_i, u = uniform from counter (id_base, 0xC0000000, 0, 0) words 0,1, and ancestor k is
+ * the first i with prefix_i > floor(((k + u) / n) Q) computed as
+ * floor((k Q + floor(u Q)) / n) in 128-bit integer arithmetic.  Returns -1 if all
+ * weights are zero or any is NaN. */
+int mlo_resample_systematic(int64_t n, const double* logw, uint64_t seed,
+                            uint64_t id_base, int64_t* ancestors);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,15 @@ def lib(extra_flags=()):
                                          P(C.c_double), P(C.c_double), C.c_double,
                                          P(_Params), P(C.c_double), P(C.c_int32)]
         L.mlo_implicit_solve.restype = C.c_int
+        L.mlo_gamma.argtypes = [C.c_double, C.c_double, C.c_uint64, C.c_uint32, C.c_uint32,
+                                P(C.c_uint32)]
+        L.mlo_gamma.restype = C.c_double
+        L.mlo_posterior_sample.argtypes = [C.c_int64, C.c_int32, P(C.c_double), C.c_int32,
+                                           P(C.c_double), C.c_int32, P(C.c_int64),
+                                           P(C.c_double), C.c_uint64, C.c_uint64,
+                                           P(C.c_double), P(C.c_uint32)]
+        L.mlo_resample_systematic.argtypes = [C.c_int64, P(C.c_double), C.c_uint64, C.c_uint64,
+                                              P(C.c_int64)]
         _LIBS[key] = L
     return _LIBS[key]
 
@@ -190,3 +199,35 @@ def implicit_solve(crn, theta, x, nc, P, a_x, tau, params: Params | None = None)
                                   _p(a_x, C.c_double), float(tau), C.byref(pc),
                                   _p(y, C.c_double), C.byref(its))
     return rc, y, int(its.value)
+
+
+def gamma(shape, rate, seed=0, traj_id=0, stream=0):
+    st = C.c_uint32(0)
+    return lib().mlo_gamma(float(shape), float(rate), seed, traj_id, stream, C.byref(st)), st.value
+
+
+def posterior_sample(alpha, beta, r, G, seed=0, traj_id_base=0):
+    """theta[i, j] ~ Gamma(alpha_j + r[i, j], beta_j + G[i, j]); alpha, beta: (M,) or (n, M)."""
+    r = np.ascontiguousarray(r, np.int64)
+    G = np.ascontiguousarray(G, np.float64)
+    n, M = r.shape
+    alpha = np.ascontiguousarray(alpha, np.float64)
+    beta = np.ascontiguousarray(beta, np.float64)
+    th = np.zeros((n, M))
+    st = np.zeros(n, np.uint32)
+    rc = lib().mlo_posterior_sample(n, M, _p(alpha, C.c_double), int(alpha.ndim == 2),
+                                    _p(beta, C.c_double), int(beta.ndim == 2), _p(r, C.c_int64),
+                                    _p(G, C.c_double), seed, traj_id_base, _p(th, C.c_double),
+                                    _p(st, C.c_uint32))
+    if rc != 0:
+        raise ValueError("bad arguments")
+    return th, st
+
+
+def resample_systematic(logw, seed=0, id_base=0):
+    logw = np.ascontiguousarray(logw, np.float64)
+    anc = np.zeros(logw.size, np.int64)
+    if lib().mlo_resample_systematic(logw.size, _p(logw, C.c_double), seed, id_base,
+                                     _p(anc, C.c_int64)) != 0:
+        raise ValueError("no positive weight")
+    return anc
