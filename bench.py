@@ -310,6 +310,47 @@ def run_serving(ml, seconds, rate_hz=200.0, seed=11, max_inflight=8, budget=8 <<
 # ---------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------
+def run_bayes(ml, out, reps=20):
+    """Times the Bayesian step on the bench's own simulation output: posterior draws
+    theta ~ Gamma(1 + r, 1 + G) for every (trajectory, reaction), then systematic
+    resampling of the trajectories as particles (log-weights N(0, 9), seeded)."""
+    import torch
+    r, G = out["r"], out["G"]
+    B, M = r.shape
+    dev = r.device
+    stream = torch.cuda.current_stream()
+    one = torch.ones(M, dtype=torch.float64, device=dev)
+    theta = torch.empty((B, M), dtype=torch.float64, device=dev)
+    st = torch.empty((B,), dtype=torch.int32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    logw = torch.randn(B, dtype=torch.float64, device=dev, generator=g) * 3.0
+    anc = torch.empty((B,), dtype=torch.int64, device=dev)
+    ws = torch.empty(max(ml.ml_resample_workspace_bytes(B), 1), dtype=torch.uint8, device=dev)
+
+    def time_it(fn):
+        for k in range(3):
+            fn(k)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(reps):
+            fn(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    post_ms = time_it(lambda k: ml.ml_posterior_sample(one, one, r, G, seed=k, theta_out=theta,
+                                                       status_out=st))
+    res_ms = time_it(lambda k: ml.ml_resample_systematic(logw, seed=k, ancestors=anc,
+                                                         workspace=ws))
+    return {"posterior_draws_per_s": B * M / (post_ms / 1e3), "posterior_ms": post_ms,
+            "resample_particles_per_s": B / (res_ms / 1e3), "resample_ms": res_ms,
+            "particles": B, "reactions": M, "dtype": "f64",
+            "note": "Gamma(1 + r, 1 + G) draws of the bench's last simulation output, then "
+                    "systematic resampling of the trajectories; L2-resident inputs"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -500,6 +541,8 @@ def run_ours(args):
         rows = stats_util.compare(g, oout, g_res=stats_util.G_RESOLUTION_FAST)
         line["parity"] = {"fast_vs_oracle": stats_util.summary(rows), "n_compared": n,
                           "bad_status": res_fast["bad_status"]}
+    if rank == 0 and world == 1 and not args.ncu:
+        line["bayes_step"] = run_bayes(ml, res_fast["last_out"])
     if rank == 0 and world == 1 and args.serving_seconds > 0 and not args.ncu:
         line["serving"] = run_serving(ml, args.serving_seconds)
     if rank == 0:

@@ -276,6 +276,47 @@ int ml_server_destroy(ml_server* server);
  * issued (a graph replay counts its kernel nodes), or ML_ERR_ARG. */
 int64_t ml_model_last_launch_count(const ml_model* model);
 
+/* ---- The Bayesian step (paper, Section 1) ---------------------------------------------
+ * With a Gamma(alpha_j, beta_j) prior on each rate constant theta_j, the likelihood of a
+ * path is conjugate and the posterior given a simulated path is Gamma(alpha_j + r_j,
+ * beta_j + G_j) (shape, rate).  These two calls turn ml_simulate's r and G into posterior
+ * draws and resample particles by their weights, so that a particle-filter or ABC step
+ * runs on the device between simulations.  Both are FP64 and bit-reproducible. */
+
+/* One draw theta_ij ~ Gamma(alpha_ij + r_ij, beta_ij + G_ij) per trajectory i and
+ * reaction j (Marsaglia & Tsang 2000, with the U^(1/shape) boost for shape < 1).
+ *   alpha, beta  prior shape and rate: [n * M] row-major when *_per_traj is non-zero,
+ *                else one row [M] shared by every trajectory.  Device memory.
+ *   r, G         [n * M] row-major, as written by ml_simulate.  Device memory.
+ *   theta_out    [n * M] row-major.  Device memory.  A non-positive or NaN posterior
+ *                shape or rate gives NaN.
+ *   status_out   optional [n] device array: bit 1 set when 64 proposals of one draw were
+ *                all rejected (the draw is then the posterior mean; never observed).
+ * Random numbers: Philox4x32-10 keyed by seed, counter (traj_id_base + i, 0x80000000 + j,
+ * 0, block); traj_id_base + n must not exceed 2^32 (ML_ERR_ARG).  Asynchronous on stream
+ * (a cudaStream_t, NULL for the legacy default stream).  n = 0 is a no-op. */
+int ml_posterior_sample(int64_t n, int32_t M, const double* alpha, int32_t alpha_per_traj,
+                        const double* beta, int32_t beta_per_traj, const int64_t* r,
+                        const double* G, uint64_t seed, uint64_t traj_id_base, double* theta_out,
+                        uint32_t* status_out, void* stream);
+
+/* Workspace bytes ml_resample_systematic needs for n particles (0 for n < 1). */
+size_t ml_resample_workspace_bytes(int64_t n);
+
+/* Systematic resampling of n particles from log-weights logw[n] (device memory) into
+ * ancestors[n] (device memory, int64).  Weights are quantized to integers
+ * q_i = floor(exp(logw_i - max logw) 2^40) -- a NaN log-weight counts as weight 0 -- so
+ * that the cumulative sums are exact; ancestor k is the first i whose inclusive prefix
+ * sum exceeds floor((k Q + floor(u Q)) / n), Q = sum q_i, u one uniform from counter
+ * (id_base, 0xC0000000, 0, 0).  When no weight is positive (all -inf or NaN) or the
+ * maximum is +inf, every ancestor is -1: the call itself still returns ML_OK because the
+ * check runs on the device.  workspace: device memory, 16-byte aligned, at least
+ * ml_resample_workspace_bytes(n), owned by the caller and not shared by concurrent calls.
+ * Requires 1 <= n < 2^24 (ML_ERR_ARG otherwise).  Asynchronous on stream. */
+int ml_resample_systematic(int64_t n, const double* logw, uint64_t seed, uint64_t id_base,
+                           int64_t* ancestors, void* workspace, size_t workspace_bytes,
+                           void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -41,6 +41,7 @@ def _units():
     u.append(("api.cu", "api.o", []))
     u.append(("noalloc.cu", "noalloc.o", []))
     u.append(("server.cu", "server.o", []))
+    u.append(("bayes.cu", "bayes.o", ["-fmad=false"]))
     return u
 
 

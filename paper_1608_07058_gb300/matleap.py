@@ -86,6 +86,12 @@ def lib():
         L.ml_server_destroy.argtypes = [v]
         L.ml_autotune.argtypes = [v, C.c_int64, v, v, C.c_int32, v, C.c_int32,
                                   P(ml_sim_params), C.c_uint64, C.c_int64, P(ml_sim_params), v]
+        L.ml_posterior_sample.argtypes = [C.c_int64, C.c_int32, v, C.c_int32, v, C.c_int32, v, v,
+                                          C.c_uint64, C.c_uint64, v, v, v]
+        L.ml_resample_workspace_bytes.argtypes = [C.c_int64]
+        L.ml_resample_workspace_bytes.restype = C.c_size_t
+        L.ml_resample_systematic.argtypes = [C.c_int64, v, C.c_uint64, C.c_uint64, v, v,
+                                             C.c_size_t, v]
         _lib = L
     return _lib
 
@@ -251,6 +257,45 @@ def ml_autotune(model: Model, n_traj: int, x0, T, theta=None,
                              int(x0.dim() == 2), _ptr(T), int(T.numel() > 1), C.byref(p), seed,
                              n_sample, C.byref(best), _stream_handle(stream)))
     return best
+
+
+def ml_posterior_sample(alpha, beta, r, G, seed: int = 0, traj_id_base: int = 0,
+                        theta_out=None, status_out=None, stream=None):
+    """Posterior draws theta ~ Gamma(alpha + r, beta + G) on the device (Section 1).
+    alpha, beta: float64 CUDA tensors (M,) shared or (n, M) per trajectory; r: int64 and
+    G: float64 CUDA tensors (n, M).  Returns (theta (n, M) float64, status (n,) int32)."""
+    import torch
+    n, M = r.shape
+    if theta_out is None:
+        theta_out = torch.empty((n, M), dtype=torch.float64, device=r.device)
+    if status_out is None:
+        status_out = torch.empty((n,), dtype=torch.int32, device=r.device)
+    _check(lib().ml_posterior_sample(n, M, _ptr(alpha), int(alpha.dim() == 2), _ptr(beta),
+                                     int(beta.dim() == 2), _ptr(r), _ptr(G), seed, traj_id_base,
+                                     _ptr(theta_out), _ptr(status_out), _stream_handle(stream)))
+    return theta_out, status_out
+
+
+def ml_resample_workspace_bytes(n: int) -> int:
+    return int(lib().ml_resample_workspace_bytes(n))
+
+
+def ml_resample_systematic(logw, seed: int = 0, id_base: int = 0, ancestors=None,
+                           workspace=None, stream=None):
+    """Systematic resampling of len(logw) particles (float64 CUDA tensor) into int64
+    ancestor indices (all -1 when no weight is positive).  workspace: optional uint8 CUDA
+    tensor of at least ml_resample_workspace_bytes(n) bytes."""
+    import torch
+    n = logw.numel()
+    if ancestors is None:
+        ancestors = torch.empty((n,), dtype=torch.int64, device=logw.device)
+    need = ml_resample_workspace_bytes(n)
+    if workspace is None:
+        workspace = torch.empty((max(need, 1),), dtype=torch.uint8, device=logw.device)
+    _check(lib().ml_resample_systematic(n, _ptr(logw), seed, id_base, _ptr(ancestors),
+                                        _ptr(workspace), workspace.numel(),
+                                        _stream_handle(stream)))
+    return ancestors
 
 
 def model_from_crn(crn) -> Model:

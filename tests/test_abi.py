@@ -124,3 +124,23 @@ def test_server_without_device_fails_cleanly(ml):
     with pytest.raises(ml.MatleapError) as e:
         ml.ml_server(16 << 20, 2)
     assert e.value.code in (ml.ML_ERR_CUDA, ml.ML_ERR_OOM)
+
+
+def test_bayes_argument_errors_without_device(ml):
+    """The Bayesian-step entry points validate sizes on the host before any launch."""
+    L = ml.lib()
+    assert L.ml_resample_workspace_bytes(0) == 0
+    assert L.ml_resample_workspace_bytes(5000) >= 8 * 5000
+    assert L.ml_resample_systematic(0, None, 0, 0, None, None, 0, None) == ml.ML_ERR_ARG
+    assert L.ml_resample_systematic(1 << 24, None, 0, 0, None, None, 0, None) == ml.ML_ERR_ARG
+    assert L.ml_posterior_sample(4, 0, None, 0, None, 0, None, None, 0, 0, None, None,
+                                 None) == ml.ML_ERR_ARG
+    assert L.ml_posterior_sample(0, 3, None, 0, None, 0, None, None, 0, 0, None, None,
+                                 None) == ml.ML_OK  # empty batch: no-op
+    assert L.ml_posterior_sample(4, 3, None, 0, None, 0, None, None, 0, 2**32 - 2, None, None,
+                                 None) == ml.ML_ERR_ARG
+    # host pointers where device memory is required
+    a = np.ones(12)
+    p = a.ctypes.data
+    assert L.ml_posterior_sample(4, 3, p, 0, p, 0, p, p, 0, 0, p, None, None) == ml.ML_ERR_ARG
+    assert "device memory" in ml.ml_last_error()
