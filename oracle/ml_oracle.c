@@ -641,7 +641,32 @@ typedef struct {
   double t;
   uint32_t status;
   int64_t cnt[4];
+  /* observation grid: K nondecreasing times, the next unrecorded index kn, and this
+   * trajectory's rows X_obs[k][s] */
+  const double* tobs;
+  int32_t K, kn;
+  int64_t* xobs;
 } traj_t;
+
+/* Time-grid output.  The path X(t) is right-continuous and piecewise constant: it changes
+ * only at SSA firing times and at the ends of leaps, so X(t_k) is the state after every
+ * change at a time <= t_k.  record_obs writes the current state to every pending grid
+ * point with t_k < tcut (strict) or t_k <= tcut (inclusive). */
+static void record_obs(traj_t* tr, double tcut, int inclusive) {
+  const int32_t N = tr->md->N;
+  while (tr->kn < tr->K) {
+    const double tk = tr->tobs[tr->kn];
+    if (inclusive ? !(tk <= tcut) : !(tk < tcut)) break;
+    for (int32_t s = 0; s < N; ++s) tr->xobs[(int64_t)tr->kn * N + s] = tr->x[s];
+    tr->kn += 1;
+  }
+}
+
+/* A leap may not pass the next grid point: it ends there exactly, as it does at T. */
+static double next_stop(const traj_t* tr) {
+  if (tr->kn < tr->K && tr->tobs[tr->kn] < tr->T) return tr->tobs[tr->kn];
+  return tr->T;
+}
 
 static void eval_props(traj_t* tr) {
   for (int32_t j = 0; j < tr->md->M; ++j) {
@@ -683,6 +708,7 @@ static void ssa_burst(traj_t* tr, uint32_t step, int32_t n_max, double a0) {
       return;
     }
     for (int32_t j = 0; j < M; ++j) tr->G[j] = tr->G[j] + tr->g[j] * dt;
+    record_obs(tr, tn, 0); /* grid points before the firing see the old state */
     tr->t = tn;
     double target = u2 * a0, acc = 0.0;
     int32_t pick = -1, last = -1;
@@ -698,6 +724,7 @@ static void ssa_burst(traj_t* tr, uint32_t step, int32_t n_max, double a0) {
     for (int32_t s = 0; s < N; ++s) tr->x[s] += md->nu[pick * N + s];
     tr->r[pick] += 1;
     tr->cnt[2] += 1;
+    record_obs(tr, tr->t, 1); /* a grid point at the firing time sees the new state */
   }
 }
 
@@ -716,6 +743,7 @@ static void simulate_one(traj_t* tr) {
   int64_t* xn = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
   uint32_t step = 0;
   int32_t reject_run = 0;
+  record_obs(tr, tr->t, 1); /* grid points at t = 0 see x0 */
 
   for (;;) {
     if (!(tr->t < tr->T)) break;
@@ -803,7 +831,8 @@ static void simulate_one(traj_t* tr) {
         reject_run = 0;
         break;
       }
-      double rem = tr->T - tr->t;
+      const double stop = next_stop(tr);
+      double rem = stop - tr->t;
       double tau = tau1;
       if (tau2 < tau) tau = tau2;
       int at_horizon = 0;
@@ -878,25 +907,33 @@ static void simulate_one(traj_t* tr) {
         tr->G[j] = tr->G[j] + half * (tr->g[j] + gn[j]);
       }
       for (int32_t s = 0; s < N; ++s) tr->x[s] = xn[s];
-      tr->t = at_horizon ? tr->T : tr->t + tau;
+      tr->t = at_horizon ? stop : tr->t + tau;
+      record_obs(tr, tr->t, 1);
       tr->cnt[implicit_step ? 1 : 0] += 1;
       step++;
       reject_run = 0;
       break;
     }
   }
+  /* grid points after the end (beyond T, or after a step-limit stop) see the final state */
+  record_obs(tr, INFINITY, 1);
   free(ac); free(gn); free(Pd); free(y); free(nc); free(use_im); free(pe_on);
   free(K); free(xn);
 }
 
-int mlo_simulate(int32_t N, int32_t M, const int32_t* orders, const int32_t* stoich,
-                 const double* rates, int64_t n_traj, const double* theta,
-                 const int64_t* x0, int32_t x0_per_traj, const double* T,
-                 int32_t T_per_traj, const mlo_params* p, uint64_t seed,
-                 uint64_t traj_id_base, int64_t* X_out, int64_t* r_out, double* G_out,
-                 uint32_t* status_out, int64_t* counters_out) {
+int mlo_simulate_grid(int32_t N, int32_t M, const int32_t* orders, const int32_t* stoich,
+                      const double* rates, int64_t n_traj, const double* theta,
+                      const int64_t* x0, int32_t x0_per_traj, const double* T,
+                      int32_t T_per_traj, const mlo_params* p, uint64_t seed,
+                      uint64_t traj_id_base, const double* t_obs, int32_t K, int64_t* X_obs,
+                      int64_t* X_out, int64_t* r_out, double* G_out, uint32_t* status_out,
+                      int64_t* counters_out) {
   model_t md;
   if (n_traj < 0 || !p || !x0 || !T || (!theta && !rates)) return -1;
+  if (K < 0 || (K > 0 && (!t_obs || !X_obs))) return -1;
+  for (int32_t k = 0; k < K; ++k) /* finite, >= 0, nondecreasing */
+    if (!(t_obs[k] >= 0.0) || !(t_obs[k] <= 1.0e300) || (k > 0 && t_obs[k] < t_obs[k - 1]))
+      return -1;
   if (traj_id_base + (uint64_t)n_traj > 0x100000000ULL) return -1;
   if (model_init(&md, N, M, orders, stoich) != 0) {
     model_free(&md);
@@ -925,6 +962,10 @@ int mlo_simulate(int32_t N, int32_t M, const int32_t* orders, const int32_t* sto
       tr.G[j] = 0.0;
     }
     tr.t = 0.0;
+    tr.tobs = t_obs;
+    tr.K = K;
+    tr.kn = 0;
+    tr.xobs = K > 0 ? X_obs + i * (int64_t)K * N : NULL;
     simulate_one(&tr);
     status_out[i] = tr.status;
     if (counters_out)
@@ -933,6 +974,76 @@ int mlo_simulate(int32_t N, int32_t M, const int32_t* orders, const int32_t* sto
   free(g);
   free(a);
   model_free(&md);
+  return 0;
+}
+
+int mlo_simulate(int32_t N, int32_t M, const int32_t* orders, const int32_t* stoich,
+                 const double* rates, int64_t n_traj, const double* theta,
+                 const int64_t* x0, int32_t x0_per_traj, const double* T,
+                 int32_t T_per_traj, const mlo_params* p, uint64_t seed,
+                 uint64_t traj_id_base, int64_t* X_out, int64_t* r_out, double* G_out,
+                 uint32_t* status_out, int64_t* counters_out) {
+  return mlo_simulate_grid(N, M, orders, stoich, rates, n_traj, theta, x0, x0_per_traj, T,
+                           T_per_traj, p, seed, traj_id_base, NULL, 0, NULL, X_out, r_out,
+                           G_out, status_out, counters_out);
+}
+
+/* ------------------------------------------------------------------------------------
+ * Accuracy metric (Section 3): the Kullback-Leibler divergence of a method's marginal
+ * distributions from those of exact SSA, averaged over all time points and species.
+ * The paper does not say how the empirical distributions are formed; this reading bins
+ * the integer counts of both samples on their pooled range [lo, hi] with integer width
+ * w = ceil((hi - lo + 1) / max_bins) (one count per bin while the range fits), adds 1/2
+ * to every bin of both histograms so that the divergence is finite, and computes
+ *   KL(p || q) = sum_b p_b (log p_b - log q_b),
+ *   p_b = (c_ref,b + 1/2) / (n_ref + nbins/2),  q_b = (c_test,b + 1/2) / (n_test + nbins/2),
+ * with p the exact-SSA (reference) sample.  The sum over bins and the mean over the K x N
+ * (time point, species) pairs take the canonical lane-tree order.
+ * ---------------------------------------------------------------------------------- */
+double mlo_kl_sample(int64_t n_ref, const int64_t* a, int64_t sa, int64_t n_test,
+                     const int64_t* b, int64_t sb, int32_t max_bins) {
+  int64_t lo = a[0], hi = a[0];
+  for (int64_t i = 0; i < n_ref; ++i) {
+    if (a[i * sa] < lo) lo = a[i * sa];
+    if (a[i * sa] > hi) hi = a[i * sa];
+  }
+  for (int64_t i = 0; i < n_test; ++i) {
+    if (b[i * sb] < lo) lo = b[i * sb];
+    if (b[i * sb] > hi) hi = b[i * sb];
+  }
+  const int64_t span = hi - lo + 1;
+  const int64_t w = (span + max_bins - 1) / max_bins;
+  const int64_t nbins = (hi - lo) / w + 1;
+  int64_t* ca = (int64_t*)calloc((size_t)nbins, sizeof(int64_t));
+  int64_t* cb = (int64_t*)calloc((size_t)nbins, sizeof(int64_t));
+  double* term = (double*)malloc(sizeof(double) * (size_t)nbins);
+  for (int64_t i = 0; i < n_ref; ++i) ca[(a[i * sa] - lo) / w] += 1;
+  for (int64_t i = 0; i < n_test; ++i) cb[(b[i * sb] - lo) / w] += 1;
+  const double da = (double)n_ref + 0.5 * (double)nbins;
+  const double db = (double)n_test + 0.5 * (double)nbins;
+  for (int64_t k = 0; k < nbins; ++k) {
+    const double pk = ((double)ca[k] + 0.5) / da;
+    const double qk = ((double)cb[k] + 0.5) / db;
+    term[k] = pk * (mlo_log(pk) - mlo_log(qk));
+  }
+  const double kl = mlo_lane_tree_sum(term, (int32_t)nbins);
+  free(ca);
+  free(cb);
+  free(term);
+  return kl;
+}
+
+int mlo_kl_grid(int64_t n_ref, const int64_t* X_ref, int64_t n_test, const int64_t* X_test,
+                int32_t K, int32_t N, int32_t max_bins, double* kl_out, double* kl_mean) {
+  if (n_ref < 1 || n_test < 1 || K < 1 || N < 1 || max_bins < 1 || !X_ref || !X_test ||
+      !kl_out)
+    return -1;
+  const int64_t stride = (int64_t)K * N; /* layout [n][K][N] */
+  for (int32_t k = 0; k < K; ++k)
+    for (int32_t s = 0; s < N; ++s)
+      kl_out[k * N + s] = mlo_kl_sample(n_ref, X_ref + k * N + s, stride, n_test,
+                                        X_test + k * N + s, stride, max_bins);
+  if (kl_mean) *kl_mean = mlo_lane_tree_sum(kl_out, K * N) / (double)(K * N);
   return 0;
 }
 

@@ -76,6 +76,31 @@ int mlo_simulate(int32_t N, int32_t M, const int32_t* orders, const int32_t* sto
                  uint64_t traj_id_base, int64_t* X_out, int64_t* r_out, double* G_out,
                  uint32_t* status_out, int64_t* counters_out);
 
+/* mlo_simulate with time-grid output: t_obs[K] finite, >= 0 and nondecreasing; X_obs
+ * [n_traj][K][N] receives X(t_k), the state after every change at a time <= t_k (the path
+ * is right-continuous).  Leaps end exactly at each grid point as they do at T; SSA
+ * firings are not moved.  Points beyond a trajectory's end (t_k > T, or after a step-limit
+ * stop) get its final state.  K = 0 is mlo_simulate. */
+int mlo_simulate_grid(int32_t N, int32_t M, const int32_t* orders, const int32_t* stoich,
+                      const double* rates, int64_t n_traj, const double* theta,
+                      const int64_t* x0, int32_t x0_per_traj, const double* T,
+                      int32_t T_per_traj, const mlo_params* p, uint64_t seed,
+                      uint64_t traj_id_base, const double* t_obs, int32_t K, int64_t* X_obs,
+                      int64_t* X_out, int64_t* r_out, double* G_out, uint32_t* status_out,
+                      int64_t* counters_out);
+
+/* ---- Accuracy metric (Section 3, Table 1) ------------------------------------------
+ * KL(p || q) of two integer samples (n_ref values a[i*sa], n_test values b[i*sb]):
+ * histograms on the pooled range [lo, hi] with integer bin width
+ * w = ceil((hi - lo + 1) / max_bins), 1/2 added to every bin of both, p from the
+ * reference sample; sum over bins in lane-tree order. */
+double mlo_kl_sample(int64_t n_ref, const int64_t* a, int64_t sa, int64_t n_test,
+                     const int64_t* b, int64_t sb, int32_t max_bins);
+/* kl_out[k][s] = mlo_kl_sample over time point k and species s of X_ref [n_ref][K][N] and
+ * X_test [n_test][K][N]; *kl_mean (optional) = lane-tree sum of kl_out / (K N). */
+int mlo_kl_grid(int64_t n_ref, const int64_t* X_ref, int64_t n_test, const int64_t* X_test,
+                int32_t K, int32_t N, int32_t max_bins, double* kl_out, double* kl_mean);
+
 /* Building blocks, exported so that tests can pin each one on its own. */
 void mlo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double mlo_u01_from_words(uint32_t w0, uint32_t w1);
@@ -114,8 +139,9 @@ int mlo_posterior_sample(int64_t n, int32_t M, const double* alpha, int32_t alph
  * are quantized to integers q_i = floor(w_i 2^40) (so every prefix sum is exact), Q = sum
  * q_i, u = uniform from counter (id_base, 0xC0000000, 0, 0) words 0,1, and ancestor k is
  * the first i with prefix_i > floor(((k + u) / n) Q) computed as
- * floor((k Q + floor(u Q)) / n) in 128-bit integer arithmetic.  Returns -1 if all
- * weights are zero or any is NaN. */
+ * floor((k Q + floor(u Q)) / n) in 128-bit integer arithmetic.  A NaN log-weight counts
+ * as weight 0.  Returns -1 (every ancestor -1) when no weight is positive or the maximum
+ * log-weight is +inf. */
 int mlo_resample_systematic(int64_t n, const double* logw, uint64_t seed,
                             uint64_t id_base, int64_t* ancestors);
 

@@ -61,6 +61,19 @@ def lib(extra_flags=()):
                                    C.c_uint64, C.c_uint64, P(C.c_int64), P(C.c_int64),
                                    P(C.c_double), P(C.c_uint32), P(C.c_int64)]
         L.mlo_simulate.restype = C.c_int
+        L.mlo_simulate_grid.argtypes = [C.c_int32, C.c_int32, P(C.c_int32), P(C.c_int32),
+                                        P(C.c_double), C.c_int64, P(C.c_double), P(C.c_int64),
+                                        C.c_int32, P(C.c_double), C.c_int32, P(_Params),
+                                        C.c_uint64, C.c_uint64, P(C.c_double), C.c_int32,
+                                        P(C.c_int64), P(C.c_int64), P(C.c_int64),
+                                        P(C.c_double), P(C.c_uint32), P(C.c_int64)]
+        L.mlo_simulate_grid.restype = C.c_int
+        L.mlo_kl_sample.argtypes = [C.c_int64, P(C.c_int64), C.c_int64, C.c_int64,
+                                    P(C.c_int64), C.c_int64, C.c_int32]
+        L.mlo_kl_sample.restype = C.c_double
+        L.mlo_kl_grid.argtypes = [C.c_int64, P(C.c_int64), C.c_int64, P(C.c_int64), C.c_int32,
+                                  C.c_int32, C.c_int32, P(C.c_double), P(C.c_double)]
+        L.mlo_kl_grid.restype = C.c_int
         L.mlo_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
         L.mlo_u01_from_words.argtypes = [C.c_uint32, C.c_uint32]
         L.mlo_u01_from_words.restype = C.c_double
@@ -101,9 +114,10 @@ def _p(a, ct):
 
 
 def simulate(crn, n_traj, x0, T, theta=None, params: Params | None = None, seed=0,
-             traj_id_base=0, extra_flags=()):
+             traj_id_base=0, extra_flags=(), t_obs=None):
     """Run the oracle.  x0: (N,) or (n_traj, N); T: scalar, (1,) or (n_traj,);
-    theta: None or (n_traj, M).  Returns dict X, r, G, status, counters."""
+    theta: None or (n_traj, M); t_obs: None or (K,) observation times.  Returns dict X, r,
+    G, status, counters, and X_obs (n_traj, K, N) when t_obs is given."""
     L = lib(extra_flags)
     params = params or Params()
     N, M = crn.n_species, crn.n_reactions
@@ -119,17 +133,49 @@ def simulate(crn, n_traj, x0, T, theta=None, params: Params | None = None, seed=
     G = np.zeros((n_traj, M), np.float64)
     st = np.zeros(n_traj, np.uint32)
     cnt = np.zeros((n_traj, 4), np.int64)
+    K = 0 if t_obs is None else int(np.size(t_obs))
+    tk = None if t_obs is None else np.ascontiguousarray(np.atleast_1d(t_obs), np.float64)
+    Xo = np.zeros((n_traj, K, N), np.int64) if t_obs is not None else None
     pc = params.c()
-    rc = L.mlo_simulate(N, M, _p(crn.orders, C.c_int32), _p(crn.stoich, C.c_int32),
-                        _p(crn.rates, C.c_double), n_traj,
-                        _p(theta, C.c_double) if theta is not None else None,
-                        _p(x0, C.c_int64), x0_per, _p(T, C.c_double), T_per,
-                        C.byref(pc), seed, traj_id_base, _p(X, C.c_int64),
-                        _p(r, C.c_int64), _p(G, C.c_double), _p(st, C.c_uint32),
-                        _p(cnt, C.c_int64))
+    rc = L.mlo_simulate_grid(N, M, _p(crn.orders, C.c_int32), _p(crn.stoich, C.c_int32),
+                             _p(crn.rates, C.c_double), n_traj,
+                             _p(theta, C.c_double) if theta is not None else None,
+                             _p(x0, C.c_int64), x0_per, _p(T, C.c_double), T_per,
+                             C.byref(pc), seed, traj_id_base,
+                             _p(tk, C.c_double) if K else None, K,
+                             _p(Xo, C.c_int64) if K else None, _p(X, C.c_int64),
+                             _p(r, C.c_int64), _p(G, C.c_double), _p(st, C.c_uint32),
+                             _p(cnt, C.c_int64))
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
-    return {"X": X, "r": r, "G": G, "status": st, "counters": cnt}
+    out = {"X": X, "r": r, "G": G, "status": st, "counters": cnt}
+    if t_obs is not None:
+        out["X_obs"] = Xo
+    return out
+
+
+def kl_sample(a, b, max_bins=1024):
+    """KL(p_a || q_b) of two integer samples under the binned, half-count-smoothed reading."""
+    a = np.ascontiguousarray(a, np.int64)
+    b = np.ascontiguousarray(b, np.int64)
+    return lib().mlo_kl_sample(a.size, _p(a, C.c_int64), 1, b.size, _p(b, C.c_int64), 1,
+                               max_bins)
+
+
+def kl_grid(X_ref, X_test, max_bins=1024):
+    """Per (time point, species) KL of X_test's marginals from X_ref's, both (n, K, N);
+    returns (kl (K, N), mean)."""
+    X_ref = np.ascontiguousarray(X_ref, np.int64)
+    X_test = np.ascontiguousarray(X_test, np.int64)
+    _, K, N = X_ref.shape
+    assert X_test.shape[1:] == (K, N)
+    kl = np.zeros((K, N))
+    mean = C.c_double(0.0)
+    if lib().mlo_kl_grid(X_ref.shape[0], _p(X_ref, C.c_int64), X_test.shape[0],
+                         _p(X_test, C.c_int64), K, N, max_bins, _p(kl, C.c_double),
+                         C.byref(mean)) != 0:
+        raise ValueError("oracle rejected the arguments")
+    return kl, mean.value
 
 
 def philox(ctr, key):
