@@ -272,6 +272,41 @@ int ml_server_stats(ml_server* server, int64_t* admitted, int64_t* completed,
  * running ones and frees the server.  NULL is a no-op. */
 int ml_server_destroy(ml_server* server);
 
+/* ml_simulate with time-grid output (paper, Section 3: the accuracy study compares
+ * marginal distributions at a series of time points).  t_obs: K observation times, device
+ * memory, shared by all trajectories; they must be finite, >= 0 and nondecreasing, which
+ * the kernel checks (status ML_ST_BAD_INPUT on every trajectory otherwise, so the call
+ * stays asynchronous).  X_obs: [n_traj][K][N] int64, device memory, receives X(t_k): the
+ * path is right-continuous and piecewise constant, so X(t_k) is the state after every
+ * change at a time <= t_k.  A leap is shortened to end exactly at the next grid point (as
+ * it is at T), so a grid changes the trajectory itself; SSA firings are not moved.  Grid
+ * points beyond the trajectory's end (t_k > T, or after a step-limit stop) receive its
+ * final state.  K = 0 (t_obs, X_obs may be NULL) is ml_simulate.  Other arguments,
+ * errors and asynchrony as ml_simulate. */
+int ml_simulate_grid(const ml_model* model, int64_t n_traj, const double* theta,
+                     const int64_t* x0, int32_t x0_per_traj, const double* T,
+                     int32_t T_per_traj, const ml_sim_params* params, uint64_t seed,
+                     uint64_t traj_id_base, const double* t_obs, int32_t K, int64_t* X_obs,
+                     int64_t* X_out, int64_t* r_out, double* G_out, uint32_t* status_out,
+                     int64_t* counters_out, void* stream);
+
+/* Accuracy metric (paper, Section 3 and Table 1): the Kullback-Leibler divergence of a
+ * method's marginal distributions from those of exact SSA, per time point and species,
+ * and its average over all of them.  The paper does not define the empirical
+ * distributions; this library bins the integer counts of both samples on their pooled
+ * range [lo, hi] with integer width w = ceil((hi - lo + 1) / max_bins), adds 1/2 to every
+ * bin of both histograms, and computes KL(p || q) = sum_b p_b (log p_b - log q_b) with
+ * p_b = (c_ref,b + 1/2) / (n_ref + nbins/2) from the reference (SSA) sample and q from the
+ * test sample.  Sums over bins and the mean over the K x N pairs use a fixed order
+ * (32 lanes in index order, then a butterfly), so results are bit-reproducible.
+ *   X_ref [n_ref][K][N], X_test [n_test][K][N]: int64 device memory (ml_simulate_grid's
+ *   X_obs layout).  kl_out [K][N] double, device memory.  kl_mean_out: optional device
+ *   double.  1 <= max_bins <= 4096; n_ref, n_test >= 1 and below 2^31.
+ * Asynchronous on stream; argument errors as ML_ERR_ARG before any launch. */
+int ml_kl_divergence(int64_t n_ref, const int64_t* X_ref, int64_t n_test,
+                     const int64_t* X_test, int32_t K, int32_t N, int32_t max_bins,
+                     double* kl_out, double* kl_mean_out, void* stream);
+
 /* Number of kernel launches the last ml_simulate/ml_simulate_host call on this model
  * issued (a graph replay counts its kernel nodes), or ML_ERR_ARG. */
 int64_t ml_model_last_launch_count(const ml_model* model);

@@ -42,6 +42,7 @@ def _units():
     u.append(("noalloc.cu", "noalloc.o", []))
     u.append(("server.cu", "server.o", []))
     u.append(("bayes.cu", "bayes.o", ["-fmad=false"]))
+    u.append(("metrics.cu", "metrics.o", ["-fmad=false"]))
     return u
 
 

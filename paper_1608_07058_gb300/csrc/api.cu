@@ -253,6 +253,29 @@ mlk::KernelEntry warp_entry(int precision) {
   return precision == ML_PREC_FAST_FP32 ? mlk::warp_entry_fast() : mlk::warp_entry_ref();
 }
 
+// Time-grid output: the sequential driver's grid build (thread shapes) or the warp
+// kernel's grid build.
+mlk::KernelEntry thread_seq_grid_entry(int precision, int variant) {
+  if (precision == ML_PREC_FAST_FP32) {
+    switch (variant) {
+      case 0: return mlk::thread_seq_grid_entry_fast_0();
+      case 1: return mlk::thread_seq_grid_entry_fast_1();
+      case 2: return mlk::thread_seq_grid_entry_fast_2();
+      default: return mlk::thread_seq_grid_entry_fast_3();
+    }
+  }
+  switch (variant) {
+    case 0: return mlk::thread_seq_grid_entry_ref_0();
+    case 1: return mlk::thread_seq_grid_entry_ref_1();
+    case 2: return mlk::thread_seq_grid_entry_ref_2();
+    default: return mlk::thread_seq_grid_entry_ref_3();
+  }
+}
+
+mlk::KernelEntry warp_grid_entry(int precision) {
+  return precision == ML_PREC_FAST_FP32 ? mlk::warp_grid_entry_fast() : mlk::warp_grid_entry_ref();
+}
+
 bool is_device_pointer(const void* p) {
   if (!p) return false;
   cudaPointerAttributes at;
@@ -344,6 +367,7 @@ int ensure_tables(ml_model* m, DeviceState& st, int shape, int variant) {
 struct Plan {
   bool occ = false;
   bool seq = false;
+  bool grid_out = false;  // kernel build with time-grid output
   int shape = ML_SHAPE_THREAD;
   int variant = 0;
   mlk::KernelEntry entry{};
@@ -355,7 +379,7 @@ struct Plan {
 
 // Chooses the kernel and launch shape for one call (model lock held).
 int make_plan(ml_model* m, DeviceState& st, const ml_sim_params& p, int64_t n_traj,
-              Plan* plan) {
+              Plan* plan, bool grid_out = false) {
   int shape = p.shape;
   const int variant = thread_variant_for(*m);
   auto tk = st.tuned.find({p.precision, p.form});
@@ -365,9 +389,12 @@ int make_plan(ml_model* m, DeviceState& st, const ml_sim_params& p, int64_t n_tr
                                   : (variant >= 0 ? ML_SHAPE_THREAD : ML_SHAPE_WARP);
   }
   const int req_shape = shape;
-  const bool occ = (shape == ML_SHAPE_THREAD_OCC || shape == ML_SHAPE_THREAD_SEQ_OCC) &&
+  // a call with time-grid output runs the grid build of the sequential driver (the
+  // drivers give identical results), without the occupancy bound
+  const bool occ = !grid_out &&
+                   (shape == ML_SHAPE_THREAD_OCC || shape == ML_SHAPE_THREAD_SEQ_OCC) &&
                    p.precision == ML_PREC_FAST_FP32;
-  const bool seq = shape == ML_SHAPE_THREAD_SEQ || shape == ML_SHAPE_THREAD_SEQ_OCC;
+  const bool seq = grid_out || shape == ML_SHAPE_THREAD_SEQ || shape == ML_SHAPE_THREAD_SEQ_OCC;
   if (shape != ML_SHAPE_WARP) shape = ML_SHAPE_THREAD;
   if (shape == ML_SHAPE_THREAD && variant < 0)
     return fail(ML_ERR_UNSUPPORTED, "model %dx%d is too large for one thread per trajectory",
@@ -375,7 +402,9 @@ int make_plan(ml_model* m, DeviceState& st, const ml_sim_params& p, int64_t n_tr
   if (shape == ML_SHAPE_WARP && !warp_fits(*m))
     return fail(ML_ERR_UNSUPPORTED, "model %dx%d is too large for the warp kernel", m->N, m->M);
   const mlk::KernelEntry entry =
-      shape == ML_SHAPE_THREAD
+      grid_out ? (shape == ML_SHAPE_THREAD ? thread_seq_grid_entry(p.precision, variant)
+                                           : warp_grid_entry(p.precision))
+      : shape == ML_SHAPE_THREAD
           ? (seq ? thread_seq_entry(p.precision, variant, occ)
                  : thread_entry(p.precision, variant, occ))
           : warp_entry(p.precision);
@@ -386,6 +415,7 @@ int make_plan(ml_model* m, DeviceState& st, const ml_sim_params& p, int64_t n_tr
   plan->shape = shape;
   plan->occ = occ;
   plan->seq = seq;
+  plan->grid_out = grid_out;
   plan->variant = variant;
   plan->entry = entry;
   plan->tables = shape == ML_SHAPE_THREAD ? st.thread_tables[variant] : st.warp_tables;
@@ -466,7 +496,8 @@ void fill_args(const ml_model* m, const ml_sim_params& p, int64_t n_traj, const 
 // updated in place when they change.
 int launch_graph(DeviceState& st, const ml_sim_params& p, const Plan& plan,
                  mlk::SimArgs& a, cudaStream_t stream) {
-  const int key2 = plan.shape == ML_SHAPE_THREAD ? plan.variant + (plan.occ ? 50 : 0) + (plan.seq ? 25 : 0) : 100;
+  const int key2 = (plan.shape == ML_SHAPE_THREAD ? plan.variant + (plan.occ ? 50 : 0) + (plan.seq ? 25 : 0) : 100) +
+                   (plan.grid_out ? 1000 : 0);
   GraphCache& gc = st.graphs[{p.precision, key2}];
   const void* tables = plan.tables;
   void* kargs[2] = {const_cast<void**>(&tables), &a};
@@ -748,8 +779,24 @@ int ml_simulate(const ml_model* cm, int64_t n_traj, const double* theta, const i
                 int32_t x0_per_traj, const double* T, int32_t T_per_traj,
                 const ml_sim_params* pp, uint64_t seed, uint64_t id_base, int64_t* X,
                 int64_t* r, double* G, uint32_t* status, int64_t* counters, void* stream) {
+  return ml_simulate_grid(cm, n_traj, theta, x0, x0_per_traj, T, T_per_traj, pp, seed, id_base,
+                          nullptr, 0, nullptr, X, r, G, status, counters, stream);
+}
+
+int ml_simulate_grid(const ml_model* cm, int64_t n_traj, const double* theta,
+                     const int64_t* x0, int32_t x0_per_traj, const double* T,
+                     int32_t T_per_traj, const ml_sim_params* pp, uint64_t seed,
+                     uint64_t id_base, const double* t_obs, int32_t K, int64_t* X_obs,
+                     int64_t* X, int64_t* r, double* G, uint32_t* status, int64_t* counters,
+                     void* stream) {
   int rc = check_sizes(cm, n_traj, id_base);
   if (rc != ML_OK) return rc;
+  if (K < 0) return fail(ML_ERR_ARG, "K must be >= 0");
+  if (K > 0 && n_traj > 0) {
+    if (!t_obs || !X_obs) return fail(ML_ERR_ARG, "t_obs and X_obs must not be NULL when K > 0");
+    if (!is_device_pointer(t_obs) || !is_device_pointer(X_obs))
+      return fail(ML_ERR_ARG, "t_obs and X_obs must be device memory of the current device");
+  }
   ml_model* m = const_cast<ml_model*>(cm);
   ml_sim_params p;
   if (pp) p = *pp;
@@ -779,11 +826,16 @@ int ml_simulate(const ml_model* cm, int64_t n_traj, const double* theta, const i
   rc = device_state(m, &st, &dev);
   if (rc != ML_OK) return rc;
   Plan plan;
-  rc = make_plan(m, *st, p, n_traj, &plan);
+  rc = make_plan(m, *st, p, n_traj, &plan, K > 0 && n_traj > 0);
   if (rc != ML_OK) return rc;
   mlk::SimArgs a;
   fill_args(m, p, n_traj, theta, x0, x0_per_traj, T, T_per_traj, seed, id_base, X, r, G,
             status, counters, &a);
+  if (K > 0) {
+    a.t_obs = t_obs;
+    a.X_obs = X_obs;
+    a.K_obs = K;
+  }
   return run_plan(m, *st, p, plan, a, static_cast<cudaStream_t>(stream));
 }
 

@@ -3,7 +3,8 @@
 //   ML_VARIANT: index into the (species, reactions) capacity table;
 //   ML_THREAD_MIN_BLOCKS = 2 (fast only): the occupancy build (at most 128 threads per
 //   CTA, about 168 registers, more resident warps, some spilling), offered to the
-//   autotuner as a separate shape.
+//   autotuner as a separate shape.  The plain builds also carry the sequential driver
+//   with time-grid output.
 #include "thread_core.cuh"
 
 #ifndef ML_VARIANT
@@ -39,8 +40,22 @@ cudaError_t launch_seq(const void* dm, const SimArgs& a, int grid, int block, si
       static_cast<const ThreadModel<kNM, kMM>*>(dm), a);
   return cudaGetLastError();
 }
+#if !(ML_FAST && ML_THREAD_MIN_BLOCKS == 2)
+cudaError_t launch_seq_grid(const void* dm, const SimArgs& a, int grid, int block, size_t smem,
+                            cudaStream_t s) {
+  k_thread_seq<kNM, kMM, Prec, true><<<grid, block, smem, s>>>(
+      static_cast<const ThreadModel<kNM, kMM>*>(dm), a);
+  return cudaGetLastError();
+}
+#endif
 }  // namespace
 
+#if !(ML_FAST && ML_THREAD_MIN_BLOCKS == 2)
+KernelEntry ML_CAT(thread_seq_grid_entry_, ML_PNAME, ML_VARIANT)() {
+  return KernelEntry{&launch_seq_grid,
+                     reinterpret_cast<const void*>(&k_thread_seq<kNM, kMM, Prec, true>)};
+}
+#endif
 KernelEntry ML_CAT(thread_entry_, ML_PNAME, ML_VARIANT)() {
   return KernelEntry{&launch, reinterpret_cast<const void*>(&k_thread<kNM, kMM, Prec>)};
 }

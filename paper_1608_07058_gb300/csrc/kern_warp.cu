@@ -1,5 +1,6 @@
 // One-trajectory-per-warp kernel for one arithmetic:
-//   ML_FAST = 0: reference precision (compile with -fmad=false), 1: fast precision.
+//   ML_FAST = 0: reference precision (compile with -fmad=false), 1: fast precision;
+//   each with and without time-grid output.
 #include "warp_core.cuh"
 
 namespace mlk {
@@ -15,15 +16,26 @@ cudaError_t launch(const void* dm, const SimArgs& a, int grid, int block, size_t
   k_warp<WPrec><<<grid, block, smem, s>>>(static_cast<const WarpModel*>(dm), a);
   return cudaGetLastError();
 }
+cudaError_t launch_grid(const void* dm, const SimArgs& a, int grid, int block, size_t smem,
+                        cudaStream_t s) {
+  k_warp<WPrec, true><<<grid, block, smem, s>>>(static_cast<const WarpModel*>(dm), a);
+  return cudaGetLastError();
+}
 }  // namespace
 
 #if ML_FAST
 KernelEntry warp_entry_fast() {
   return KernelEntry{&launch, reinterpret_cast<const void*>(&k_warp<WPrec>)};
 }
+KernelEntry warp_grid_entry_fast() {
+  return KernelEntry{&launch_grid, reinterpret_cast<const void*>(&k_warp<WPrec, true>)};
+}
 #else
 KernelEntry warp_entry_ref() {
   return KernelEntry{&launch, reinterpret_cast<const void*>(&k_warp<WPrec>)};
+}
+KernelEntry warp_grid_entry_ref() {
+  return KernelEntry{&launch_grid, reinterpret_cast<const void*>(&k_warp<WPrec, true>)};
 }
 size_t warp_smem_bytes(int warps, int N, int M, int precision) {
   const int rbytes = precision == ML_PREC_FAST_FP32 ? 4 : 8;

@@ -104,6 +104,11 @@ struct SimArgs {
   int32_t jacobian;  // ML_JAC_*
   // persistent form: next unclaimed trajectory (zeroed before each launch)
   unsigned long long* queue;
+  // time-grid output: K_obs observation times (nondecreasing, >= 0, finite; checked on the
+  // device, BAD_INPUT otherwise) and X_obs [n_traj][K_obs][N]; K_obs = 0 records nothing
+  const double* t_obs;
+  int64_t* X_obs;
+  int32_t K_obs;
 };
 
 // One compiled kernel variant: its launcher and its function pointer (for occupancy
@@ -141,9 +146,21 @@ KernelEntry thread_seq_entry_fastocc_0();
 KernelEntry thread_seq_entry_fastocc_1();
 KernelEntry thread_seq_entry_fastocc_2();
 KernelEntry thread_seq_entry_fastocc_3();
-// Warp-per-trajectory kernels (kern_warp.cu, one object per precision).
+// Sequential driver with time-grid output (reference and fast builds).
+KernelEntry thread_seq_grid_entry_ref_0();
+KernelEntry thread_seq_grid_entry_ref_1();
+KernelEntry thread_seq_grid_entry_ref_2();
+KernelEntry thread_seq_grid_entry_ref_3();
+KernelEntry thread_seq_grid_entry_fast_0();
+KernelEntry thread_seq_grid_entry_fast_1();
+KernelEntry thread_seq_grid_entry_fast_2();
+KernelEntry thread_seq_grid_entry_fast_3();
+// Warp-per-trajectory kernels (kern_warp.cu, one object per precision), without and with
+// time-grid output.
 KernelEntry warp_entry_ref();
 KernelEntry warp_entry_fast();
+KernelEntry warp_grid_entry_ref();
+KernelEntry warp_grid_entry_fast();
 // Dynamic shared memory of the warp kernel for a CTA of `warps` warps.
 size_t warp_smem_bytes(int warps, int N, int M, int precision);
 

@@ -507,7 +507,9 @@ struct ThreadTraj {
 // decision) or a bounded slice of its SSA burst.  Finished lanes refill from the work
 // queue inside the loop (persistent form).  Each lane performs exactly the arithmetic of
 // the sequential algorithm, so results do not depend on the schedule.
-template <int NM, int MM, class P>
+// kGrid: time-grid output compiled in.  Without it the grid code is absent, so the
+// kernels that serve calls without a grid are exactly the plain simulation.
+template <int NM, int MM, class P, bool kGrid = false>
 struct ThreadLane {
   using R = typename P::R;
   using TT = ThreadTraj<NM, MM, P>;
@@ -517,6 +519,7 @@ struct ThreadLane {
   long long i;
   uint32_t id, status, step;
   int reject_run, mode;
+  int kobs;  // next unrecorded grid point
   double t, T;
   R th[MM];
   long long x[NM];
@@ -557,15 +560,63 @@ struct ThreadLane {
     t = 0.0;
     step = 0;
     reject_run = 0;
+    if (kGrid) kobs = 0;
+    if (kGrid && A.K_obs > 0 && !grid_ok(A)) bad = true;
     if (bad) {
       status |= ML_ST_BAD_INPUT;
       t = T;
     }
     if (T != T) t = 0.0;  // NaN horizon: finishes at once
     mode = kEval;
+    if (kGrid && A.K_obs > 0) record(A, t, true);  // grid points at t = 0 see x0
+  }
+
+  // Time-grid output.  The path is right-continuous and piecewise constant (it changes
+  // at SSA firings and at the ends of leaps), so X(t_k) is the state after every change
+  // at a time <= t_k.  Writes the current state to each pending point with t_k < tcut
+  // (strict) or t_k <= tcut (inclusive).
+  __device__ __forceinline__ void record(const SimArgs& A, double tcut, bool inclusive) {
+    while (kobs < A.K_obs) {
+      const double tk = __ldg(A.t_obs + kobs);
+      if (inclusive ? !(tk <= tcut) : !(tk < tcut)) break;
+      int64_t* o = A.X_obs + ((long long)i * A.K_obs + kobs) * A.N;
+#pragma unroll
+      for (int s = 0; s < NM; ++s)
+        if (s < A.N) o[s] = x[s];
+      ++kobs;
+    }
+  }
+
+  // A leap ends exactly at the next grid point, as it does at T.
+  __device__ __forceinline__ double stop_time(const SimArgs& A) const {
+    if (kobs < A.K_obs) {
+      const double tk = __ldg(A.t_obs + kobs);
+      if (tk < T) return tk;
+    }
+    return T;
+  }
+
+  __device__ static bool grid_ok(const SimArgs& A) {
+    double prev = 0.0;
+    for (int k = 0; k < A.K_obs; ++k) {
+      const double tk = __ldg(A.t_obs + k);
+      if (!(tk >= prev) || !(tk <= 1.0e300)) return false;
+      prev = tk;
+    }
+    return true;
   }
 
   __device__ __forceinline__ void finish(const SimArgs& A, bool staged) {
+    // grid points past the end (beyond T, after a step-limit stop, or all of a rejected
+    // grid) see the final state
+    if (kGrid) {
+      for (; kobs < A.K_obs; ++kobs) {
+        int64_t* o = A.X_obs + ((long long)i * A.K_obs + kobs) * A.N;
+#pragma unroll
+        for (int s = 0; s < NM; ++s)
+          if (s < A.N) o[s] = x[s];
+      }
+    }
 #pragma unroll
     for (int s = 0; s < NM; ++s)
       if (s < A.N) A.X[i * A.N + s] = x[s];
@@ -629,6 +680,7 @@ struct ThreadLane {
         }
 #pragma unroll
         for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)g[j] * (double)dt;
+        if (kGrid && A.K_obs > 0) record(A, tn, false);  // points before the firing: old state
         t = tn;
       } else {
         const float dt = (float)(-P::log(P::u(w, 0)) / a0);
@@ -639,6 +691,7 @@ struct ThreadLane {
 #pragma unroll
         for (int j = 0; j < MM; ++j) kahan_add(Gs[j], Gc[j], (float)g[j] * dt);
         kahan_add(el, elc, dt);
+        if (kGrid && A.K_obs > 0) record(A, t + ((double)el - (double)elc), false);
       }
       const int pick = TT::pick_reaction(a, w);
 #pragma unroll
@@ -646,6 +699,8 @@ struct ThreadLane {
 #pragma unroll
       for (int j = 0; j < MM; ++j) r[j] += (j == pick) ? 1 : 0;
       cnt[2] += 1;
+      if (kGrid && A.K_obs > 0)  // a point at the firing time: new state
+        record(A, P::kRef ? t : t + ((double)el - (double)elc), true);
       if (++b >= n_max) {
         burst_over = true;
         break;
@@ -768,7 +823,8 @@ struct ThreadLane {
           burst = implicit ? A.n_ssa_im : A.n_ssa_ex;
           break;
         }
-        const double rm = T - t;
+        const double stop = kGrid ? stop_time(A) : T;
+        const double rm = stop - t;
         R tau = tau1;
         if (tau2 < tau) tau = tau2;
         bool at_horizon = false;
@@ -844,7 +900,8 @@ struct ThreadLane {
         }
 #pragma unroll
         for (int s = 0; s < NM; ++s) x[s] = xn[s];
-        t = at_horizon ? T : t + (double)tau;
+        t = at_horizon ? stop : t + (double)tau;
+        if (kGrid && A.K_obs > 0) record(A, t, true);
         cnt[implicit_step ? 1 : 0] += 1;
         step++;
         reject_run = 0;
@@ -906,14 +963,15 @@ __global__ void ML_THREAD_BOUNDS k_thread(const ThreadModel<NM, MM>* __restrict_
 // Sequential per-lane driver over the same lane state machine: each thread runs its
 // trajectory to the end (whole SSA bursts at once) before claiming the next one.  It has
 // less scheduling overhead and suits leap-dominated workloads; the autotuner picks between
-// the two drivers.
-template <int NM, int MM, class P>
+// the two drivers.  Its kGrid build serves every thread-shape call with time-grid output
+// (the two drivers give identical results).
+template <int NM, int MM, class P, bool kGrid = false>
 __global__ void ML_THREAD_BOUNDS k_thread_seq(const ThreadModel<NM, MM>* __restrict__ gmd,
                                               const SimArgs args) {
   __shared__ ThreadModel<NM, MM> smd;
   __shared__ uint64_t mbar;
   const bool staged = stage_model_bulk(&smd, gmd, (uint32_t)thread_model_bytes<NM, MM>(), &mbar);
-  using Lane = ThreadLane<NM, MM, P>;
+  using Lane = ThreadLane<NM, MM, P, kGrid>;
   Lane L;
   long long i = args.queue ? (long long)atomicAdd(args.queue, 1ULL)
                            : (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -394,6 +394,8 @@ struct WarpTraj {
     return 1;
   }
 
+  // kGrid: time-grid output compiled in (absent from the build that serves plain calls).
+  template <bool kGrid>
   __device__ static void run(const WarpModel& md, const WarpSlab& sl, const SimArgs& A,
                              long long i, int lane) {
     const int N = md.N, M = md.M;
@@ -423,6 +425,15 @@ struct WarpTraj {
         if (x0[s] < 0) bad = true;
       }
     }
+    // a malformed observation grid (not finite, negative or decreasing) is bad input
+    if (kGrid && A.K_obs > 0 && lane == 0) {
+      double prev = 0.0;
+      for (int k = 0; k < A.K_obs; ++k) {
+        const double tk = A.t_obs[k];
+        if (!(tk >= prev) || !(tk <= 1.0e300)) bad = true;
+        prev = tk;
+      }
+    }
     bad = __any_sync(0xffffffffu, bad);
     __syncwarp();
     const double T = A.T_per ? A.T[i] : A.T[0];
@@ -443,6 +454,31 @@ struct WarpTraj {
       t = T;
     }
     if (T != T) t = 0.0;
+
+    // Time-grid output: X(t_k) of the right-continuous path; each lane writes its own
+    // species, the grid index is warp-uniform.
+    int kobs = 0;
+    auto record = [&](double tcut, bool inclusive) {
+      while (kobs < A.K_obs) {
+        const double tk = A.t_obs[kobs];
+        if (inclusive ? !(tk <= tcut) : !(tk < tcut)) break;
+        int64_t* o = A.X_obs + ((long long)i * A.K_obs + kobs) * N;
+#pragma unroll
+        for (int q = 0; q < kSPL; ++q) {
+          const int s = lane + 32 * q;
+          if (s < N) o[s] = sl.x[s];
+        }
+        ++kobs;
+      }
+    };
+    auto stop_time = [&]() -> double {
+      if (kobs < A.K_obs) {
+        const double tk = A.t_obs[kobs];
+        if (tk < T) return tk;
+      }
+      return T;
+    };
+    if (kGrid && A.K_obs > 0) record(t, true);
 
     auto eval_props = [&]() {
 #pragma unroll
@@ -487,6 +523,10 @@ struct WarpTraj {
 #pragma unroll
         for (int q = 0; q < kRPL; ++q) kahan_add(Gs[q], Gc[q], (float)g[q] * dt);
         kahan_add(el, elc, dt);
+        if (kGrid && A.K_obs > 0) {
+          record(t + ((double)el - (double)elc), false);  // before the firing: old state
+          __syncwarp();
+        }
         const int pk = pick(a_s, a, w, M, lane);
         if (pk >= 0) {
           const int e0 = md.rx_ptr[pk], e1 = md.rx_ptr[pk + 1];
@@ -497,6 +537,7 @@ struct WarpTraj {
           cnt[2] += 1;
         }
         __syncwarp();
+        if (kGrid && A.K_obs > 0) record(t + ((double)el - (double)elc), true);
       }
       const double elapsed = (double)el - (double)elc;
 #pragma unroll
@@ -544,6 +585,10 @@ struct WarpTraj {
           if (P::kRef) G[q] = G[q] + (double)g[q] * (double)dt;
           else G[q] = G[q] + (double)(g[q] * dt);  // FP32 increment, FP64 accumulation
         }
+        if (kGrid && A.K_obs > 0) {
+          record(tn, false);  // points before the firing see the old state
+          __syncwarp();
+        }
         t = tn;
         const int pk = pick(a_s, a, w, M, lane);
         if (pk >= 0) {
@@ -555,6 +600,7 @@ struct WarpTraj {
           cnt[2] += 1;
         }
         __syncwarp();
+        if (kGrid && A.K_obs > 0) record(t, true);  // a point at the firing time: new state
       }
     };
 
@@ -661,7 +707,8 @@ struct WarpTraj {
             burst = implicit ? A.n_ssa_im : A.n_ssa_ex;
             break;
           }
-          const double rem = T - t;
+          const double stop = kGrid ? stop_time() : T;
+          const double rem = stop - t;
           R tau = tau1;
           if (tau2 < tau) tau = tau2;
           bool at_horizon = false;
@@ -760,7 +807,8 @@ struct WarpTraj {
             if (s < N) sl.x[s] = sl.xn[s];
           }
           __syncwarp();
-          t = at_horizon ? T : t + (double)tau;
+          t = at_horizon ? stop : t + (double)tau;
+          if (kGrid && A.K_obs > 0) record(t, true);
           cnt[implicit_step ? 1 : 0] += 1;
           step++;
           reject_run = 0;
@@ -774,6 +822,18 @@ struct WarpTraj {
       }
     }
     status = __reduce_or_sync(0xffffffffu, status);
+    // grid points past the end (beyond T, after a step-limit stop, or all of a rejected
+    // grid): the final state
+    if (kGrid) {
+      for (; kobs < A.K_obs; ++kobs) {
+        int64_t* o = A.X_obs + ((long long)i * A.K_obs + kobs) * N;
+#pragma unroll
+        for (int q = 0; q < kSPL; ++q) {
+          const int s = lane + 32 * q;
+          if (s < N) o[s] = sl.x[s];
+        }
+      }
+    }
 #pragma unroll
     for (int q = 0; q < kSPL; ++q) {
       const int s = lane + 32 * q;
@@ -799,7 +859,7 @@ struct WarpTraj {
 // Kernel: model tables staged once per CTA into the front of dynamic shared memory, one
 // slab per warp after them.  Plain form: warp w of CTA b runs trajectory b*warps + w.
 // Persistent form: lane 0 claims the next trajectory from the device queue.
-template <class P>
+template <class P, bool kGrid = false>
 __global__ void __launch_bounds__(256) k_warp(const WarpModel* __restrict__ gmd,
                                               const SimArgs args) {
   extern __shared__ __align__(16) char smem[];
@@ -820,7 +880,7 @@ __global__ void __launch_bounds__(256) k_warp(const WarpModel* __restrict__ gmd,
     i = (long long)blockIdx.x * warps + warp;
   }
   while (i < args.n_traj) {
-    WarpTraj<P>::run(md, sl, args, i, lane);
+    WarpTraj<P>::template run<kGrid>(md, sl, args, i, lane);
     if (!staged && lane == 0) args.status[i] |= ML_ST_STAGE_TIMEOUT;
     if (!args.queue) break;
     long long c = 0;

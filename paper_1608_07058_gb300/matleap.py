@@ -86,6 +86,11 @@ def lib():
         L.ml_server_destroy.argtypes = [v]
         L.ml_autotune.argtypes = [v, C.c_int64, v, v, C.c_int32, v, C.c_int32,
                                   P(ml_sim_params), C.c_uint64, C.c_int64, P(ml_sim_params), v]
+        L.ml_simulate_grid.argtypes = [v, C.c_int64, v, v, C.c_int32, v, C.c_int32,
+                                       P(ml_sim_params), C.c_uint64, C.c_uint64, v, C.c_int32,
+                                       v, v, v, v, v, v, v]
+        L.ml_kl_divergence.argtypes = [C.c_int64, v, C.c_int64, v, C.c_int32, C.c_int32,
+                                       C.c_int32, v, v, v]
         L.ml_posterior_sample.argtypes = [C.c_int64, C.c_int32, v, C.c_int32, v, C.c_int32, v, v,
                                           C.c_uint64, C.c_uint64, v, v, v]
         L.ml_resample_workspace_bytes.argtypes = [C.c_int64]
@@ -198,6 +203,50 @@ def ml_simulate(model: Model, n_traj: int, x0, T, theta=None, params: Optional[m
                              _ptr(out["status"]), _ptr(out.get("counters")),
                              _stream_handle(stream)))
     return out
+
+
+def ml_simulate_grid(model: Model, n_traj: int, x0, T, t_obs, theta=None,
+                     params: Optional[ml_sim_params] = None, seed: int = 0,
+                     traj_id_base: int = 0, out: Optional[dict] = None, counters: bool = True,
+                     stream=None) -> dict:
+    """ml_simulate with time-grid output: t_obs is a float64 CUDA tensor (K,) of
+    nondecreasing observation times; the result adds X_obs (n_traj, K, N) int64 with the
+    state X(t_k) of every trajectory."""
+    import torch
+    dev = x0.device
+    K = int(t_obs.numel())
+    if out is None:
+        out = {"X": torch.empty((n_traj, model.N), dtype=torch.int64, device=dev),
+               "r": torch.empty((n_traj, model.M), dtype=torch.int64, device=dev),
+               "G": torch.empty((n_traj, model.M), dtype=torch.float64, device=dev),
+               "status": torch.empty((n_traj,), dtype=torch.int32, device=dev),
+               "X_obs": torch.empty((n_traj, K, model.N), dtype=torch.int64, device=dev)}
+        if counters:
+            out["counters"] = torch.empty((n_traj, 4), dtype=torch.int64, device=dev)
+    p = params if params is not None else ml_default_params()
+    _check(lib().ml_simulate_grid(C.c_void_p(model.handle), n_traj, _ptr(theta), _ptr(x0),
+                                  int(x0.dim() == 2), _ptr(T), int(T.numel() > 1), C.byref(p),
+                                  seed, traj_id_base, _ptr(t_obs) if K else None, K,
+                                  _ptr(out["X_obs"]) if K else None, _ptr(out["X"]),
+                                  _ptr(out["r"]), _ptr(out["G"]), _ptr(out["status"]),
+                                  _ptr(out.get("counters")), _stream_handle(stream)))
+    return out
+
+
+def ml_kl_divergence(X_ref, X_test, max_bins: int = 1024, kl_out=None, kl_mean=None,
+                     stream=None):
+    """KL of X_test's marginals from X_ref's (both int64 CUDA tensors (n, K, N)) per time
+    point and species; returns (kl (K, N) float64, mean (1,) float64) CUDA tensors."""
+    import torch
+    _, K, N = X_ref.shape
+    if kl_out is None:
+        kl_out = torch.empty((K, N), dtype=torch.float64, device=X_ref.device)
+    if kl_mean is None:
+        kl_mean = torch.empty((1,), dtype=torch.float64, device=X_ref.device)
+    _check(lib().ml_kl_divergence(X_ref.shape[0], _ptr(X_ref), X_test.shape[0], _ptr(X_test),
+                                  K, N, max_bins, _ptr(kl_out), _ptr(kl_mean),
+                                  _stream_handle(stream)))
+    return kl_out, kl_mean
 
 
 def ml_simulate_noalloc(model: Model, n_traj: int, x0, T, theta=None,
