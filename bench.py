@@ -351,6 +351,76 @@ def run_bayes(ml, out, reps=20):
                     "systematic resampling of the trajectories; L2-resident inputs"}
 
 
+def run_accuracy(ml, n=10_000, K=20, replicates=5, seed=500):
+    """The accuracy study of Section 3 (Table 1) on the stiff dimerisation: per method, the
+    KL divergence of its marginals from exact SSA averaged over K time points and all
+    species (mean and std over replicates of n trajectories, each against a fresh SSA
+    reference sample), and the device time of one n-trajectory run."""
+    import numpy as np
+    import torch
+    from paper_1608_07058_gb300 import workloads as W
+    w = W.config(1, n_traj=n)
+    model = ml.model_from_crn(w.crn)
+    dev = torch.device("cuda")
+    x0 = torch.as_tensor(w.x0, device=dev)
+    T = torch.as_tensor(w.T, device=dev)
+    t_obs = torch.linspace(float(w.T[0]) / K, float(w.T[0]), K, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    methods = {"ssa": dict(mode=ml.ML_MODE_SSA_ONLY),
+               "adaptive": dict(mode=ml.ML_MODE_ADAPTIVE, jacobian=ml.ML_JAC_FD),
+               "adaptive_symbolic_jacobian": dict(mode=ml.ML_MODE_ADAPTIVE,
+                                                  jacobian=ml.ML_JAC_ANALYTIC),
+               "explicit": dict(mode=ml.ML_MODE_EXPLICIT_ONLY)}
+
+    def run(kw, sd):
+        p = ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32, form=ml.ML_FORM_PERSISTENT,
+                                 max_steps=MAX_STEPS, **kw)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = ml.ml_simulate_grid(model, n, x0, T, t_obs, params=p, seed=sd, counters=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out["X_obs"], e0.elapsed_time(e1)
+
+    run(methods["ssa"], seed - 1)  # warm-up (tables, graph-free first launch)
+    kl = {m: [] for m in methods}
+    ms = {m: [] for m in methods}
+    for rep in range(replicates):
+        ref, _ = run(methods["ssa"], seed + 1000 * rep)
+        for i, (m, kw) in enumerate(methods.items()):
+            X, t = run(kw, seed + 1000 * rep + 1 + i)
+            _, mean = ml.ml_kl_divergence(ref, X)
+            kl[m].append(mean.item())
+            ms[m].append(t)
+    # Every grid point also ends a leap, so a denser grid shortens the implicit leaps that
+    # damp the fast pair's fluctuations: the adaptive method's divergence against grid size
+    by_k = {}
+    for Kd in (K, 10 * K, 100 * K):
+        td = torch.linspace(float(w.T[0]) / Kd, float(w.T[0]), Kd, dtype=torch.float64,
+                            device=dev)
+        outs = []
+        for kw, sd in ((methods["ssa"], seed + 7), (methods["adaptive"], seed + 8)):
+            p = ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32,
+                                     form=ml.ML_FORM_PERSISTENT, max_steps=MAX_STEPS, **kw)
+            outs.append(ml.ml_simulate_grid(model, n, x0, T, td, params=p, seed=sd + Kd))
+        kls, mean = ml.ml_kl_divergence(outs[0]["X_obs"], outs[1]["X_obs"])
+        torch.cuda.synchronize()
+        sd_ratio = (outs[1]["X_obs"][:, -1].double().std(0) /
+                    outs[0]["X_obs"][:, -1].double().std(0)).cpu().numpy()
+        by_k[str(Kd)] = {"kl_mean": mean.item(),
+                         "kl_per_species": kls.mean(0).cpu().numpy().tolist(),
+                         "std_ratio_at_T_per_species": sd_ratio.tolist(),
+                         "implicit_leaps_per_traj": float(outs[1]["counters"][:, 1].double().mean())}
+    return {m: {"kl_mean": float(np.mean(kl[m])), "kl_std": float(np.std(kl[m])),
+                "ms_per_run": float(np.median(ms[m]))} for m in methods} | {
+        "adaptive_vs_grid_points": by_k,
+        "setup": (
+        f"dimerisation x0 = (400, 798, 0), T = 0.2, eps = 0.03, {n} trajectories per "
+        f"run, {K} time points, {replicates} replicates, each against a fresh exact-SSA "
+        "sample; fast precision; KL of binned, half-count-smoothed marginals from SSA, "
+        "averaged over time points and species (Section 3, Table 1)")}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -543,6 +613,7 @@ def run_ours(args):
                           "bad_status": res_fast["bad_status"]}
     if rank == 0 and world == 1 and not args.ncu:
         line["bayes_step"] = run_bayes(ml, res_fast["last_out"])
+        line["accuracy"] = run_accuracy(ml)
     if rank == 0 and world == 1 and args.serving_seconds > 0 and not args.ncu:
         line["serving"] = run_serving(ml, args.serving_seconds)
     if rank == 0:
