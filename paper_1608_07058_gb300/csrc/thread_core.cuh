@@ -55,6 +55,17 @@ __device__ __forceinline__ T comb_factor_deriv(T v, int m) {
   return ((T(3) * (v * v) - T(6) * v) + T(2)) / T(6);
 }
 
+// C(x + z, m) - C(x, m) written as z times a polynomial, so that no two large nearby
+// values are subtracted: m = 2: z (2x + z - 1) / 2; m = 3 with u = x + z:
+// z (u^2 + u x + x^2 - 3 (u + x) + 2) / 6.
+template <class R>
+__device__ __forceinline__ R comb_diff(R xv, R z, int m) {
+  if (m == 1) return z;
+  if (m == 2) return (z * ((R(2) * xv + z) - R(1))) * R(0.5);
+  const R u = xv + z;
+  return (z * (((u * u + u * xv) + xv * xv) - R(3) * (u + xv) + R(2))) / R(6);
+}
+
 // Double-float (hi + lo FP32 pair) arithmetic for the fast-precision reaction pick: sums
 // by TwoSum (Knuth) renormalized with Fast2Sum, about 46 significant bits, all on the
 // FP32 pipe.
@@ -465,6 +476,162 @@ struct ThreadTraj {
     return 1;
   }
 
+  // g_j(x + z) - g_j(x) over the reactant species in increasing s, by the recursion
+  // D <- f(u) D + (f(u) - f(x)) B, B <- f(x) B with f = C(., m_js), u = x + z.
+  __device__ static __forceinline__ R g_diff(const Model& md, int j, const R (&xf)[NM],
+                                             const R (&z)[NM]) {
+    R D = R(0), B = R(1);
+#pragma unroll
+    for (int s = 0; s < NM; ++s) {
+      const int m = md.ord[j][s];
+      if (m != 0) {
+        D = comb_factor<R>(xf[s] + z[s], m) * D + comb_diff<R>(xf[s], z[s], m) * B;
+        B = comb_factor<R>(xf[s], m) * B;
+      }
+    }
+    return D;
+  }
+
+  // Fast precision: the implicit leap for the increment z = y - x, entirely in FP32.  The
+  // equation z = c + tau sum_j nu_j theta_j (g_j(x + z) - g_j(x)), c_s = sum_j nu_js P_j
+  // (an exact integer sum), has no cancellation between propensities of size a tau: the
+  // differences of the binomial factors are polynomials in z.  So FP32 keeps the firing
+  // counts K_j = P_j + round(tau theta_j (g_j(x + z) - g_j(x))) within rounding of the
+  // FP64 solution (on dimerisation states one leap in about 200 differs by one firing,
+  // with no preferred sign).  The stopping test uses max(tol, 1e-6) (FP32 cannot resolve
+  // 1e-10), and a forward-difference step of at least 2^-11 relative.  On success K holds
+  // the counts.  Returns 0 converged, 1 not converged, 2 singular.
+  __device__ static __forceinline__ int implicit_solve_fast(const Model& md, const R (&th)[MM],
+                                            const long long (&x)[NM], uint32_t nc,
+                                            long long (&K)[MM], R tau,
+                                            double tol, int maxit, double fd_h,
+                                            bool analytic) {
+    R xf[NM], z[NM], c[NM];
+#pragma unroll
+    for (int s = 0; s < NM; ++s) {
+      xf[s] = (R)x[s];
+      z[s] = R(0);
+      long long cs = 0;
+#pragma unroll
+      for (int j = 0; j < MM; ++j)
+        if ((nc >> j) & 1u) cs += (long long)md.nu[j][s] * K[j];
+      c[s] = (R)cs;
+    }
+    const R tolr = tol > 1e-6 ? (R)tol : R(1e-6);
+    const R hrel = fd_h > 0x1p-11 ? (R)fd_h : R(0x1p-11);
+    for (int it = 0; it < maxit; ++it) {
+      R dg[MM];
+#pragma unroll
+      for (int j = 0; j < MM; ++j) dg[j] = ((nc >> j) & 1u) ? g_diff(md, j, xf, z) : R(0);
+      R A[NM][NM], b[NM], yr[NM];
+#pragma unroll
+      for (int s = 0; s < NM; ++s) {
+        R acc = R(0);
+#pragma unroll
+        for (int j = 0; j < MM; ++j) {
+          const int v = md.nu[j][s];
+          if (((nc >> j) & 1u) && v != 0) acc = acc + (R)v * (th[j] * dg[j]);
+        }
+        b[s] = -((z[s] - c[s]) - tau * acc);
+        yr[s] = xf[s] + z[s];
+      }
+#pragma unroll
+      for (int q = 0; q < NM; ++q) {
+        R Dq[MM];
+        if (analytic) {
+#pragma unroll
+          for (int j = 0; j < MM; ++j)
+            Dq[j] = (((nc >> j) & 1u) && md.ord[j][q] != 0)
+                        ? th[j] * g_real_deriv<R>(md, j, yr, q)
+                        : R(0);
+        } else {
+          const R aq = fabs(yr[q]);
+          R zq[NM];
+#pragma unroll
+          for (int s = 0; s < NM; ++s) zq[s] = z[s];
+          zq[q] = z[q] + hrel * (aq > R(1) ? aq : R(1));
+          const R he = zq[q] - z[q];
+#pragma unroll
+          for (int j = 0; j < MM; ++j)
+            Dq[j] = (((nc >> j) & 1u) && md.ord[j][q] != 0)
+                        ? th[j] * ((g_diff(md, j, xf, zq) - dg[j]) / he)
+                        : R(0);
+        }
+#pragma unroll
+        for (int s = 0; s < NM; ++s) {
+          R acc = R(0);
+#pragma unroll
+          for (int j = 0; j < MM; ++j) {
+            const int v = md.nu[j][s];
+            if (((nc >> j) & 1u) && v != 0 && md.ord[j][q] != 0) acc = acc + (R)v * Dq[j];
+          }
+          A[s][q] = (s == q ? R(1) : R(0)) - tau * acc;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NM; ++k) {
+        int piv = k;
+        R best = fabs(A[k][k]);
+#pragma unroll
+        for (int i = k + 1; i < NM; ++i) {
+          if (fabs(A[i][k]) > best) {
+            best = fabs(A[i][k]);
+            piv = i;
+          }
+        }
+        if (!(best > R(0))) return 2;
+#pragma unroll
+        for (int i = k + 1; i < NM; ++i) {
+          if (i == piv) {
+#pragma unroll
+            for (int cc = 0; cc < NM; ++cc) {
+              const R tmp = A[k][cc];
+              A[k][cc] = A[i][cc];
+              A[i][cc] = tmp;
+            }
+            const R tb = b[k];
+            b[k] = b[i];
+            b[i] = tb;
+          }
+        }
+#pragma unroll
+        for (int i = k + 1; i < NM; ++i) {
+          const R l = A[i][k] / A[k][k];
+#pragma unroll
+          for (int cc = k + 1; cc < NM; ++cc) A[i][cc] = A[i][cc] - l * A[k][cc];
+          b[i] = b[i] - l * b[k];
+        }
+      }
+      R d[NM];
+#pragma unroll
+      for (int i = NM - 1; i >= 0; --i) {
+        d[i] = b[i] / A[i][i];
+#pragma unroll
+        for (int rr = 0; rr < i; ++rr) b[rr] = b[rr] - A[rr][i] * d[i];
+      }
+      R dmax = R(0), ymax = R(0);
+#pragma unroll
+      for (int s = 0; s < NM; ++s) {
+        z[s] = z[s] + d[s];
+        if (fabs(d[s]) > dmax) dmax = fabs(d[s]);
+        const R ys = fabs(xf[s] + z[s]);
+        if (ys > ymax) ymax = ys;
+      }
+      if (!(dmax == dmax)) return 1;
+      if (dmax <= tolr * (ymax > R(1) ? ymax : R(1))) {
+#pragma unroll
+        for (int j = 0; j < MM; ++j) {
+          if ((nc >> j) & 1u) {
+            const long long kj = K[j] + llroundf(tau * (th[j] * g_diff(md, j, xf, z)));
+            K[j] = kj > 0 ? kj : 0;
+          }
+        }
+        return 0;
+      }
+    }
+    return 1;
+  }
+
   // Inverse-CDF pick of a reaction with probability v_j / sum v, from the second uniform
   // of block w (words 2, 3).  Reference: sequential prefix sums in index order (the
   // canonical order), target u * sum with the lane-tree sum.  Fast: the same search over
@@ -850,26 +1017,34 @@ struct ThreadLane {
           if ((nc >> j) & 1u)
             K[j] = poisson_draw<P>(a[j] * tau, k0, k1, id, step, (uint32_t)j, status);
         if (implicit_step) {
-          double y[NM];
-          const double taud = (double)tau;
-          const int rc = TT::implicit_solve(md, th, x, nc, K, a, taud, A.newton_tol,
-                                            A.newton_maxit, A.fd_h,
-                                            A.jacobian == ML_JAC_ANALYTIC, y);
+          int rc;
+          if constexpr (P::kRef) {
+            double y[NM];
+            const double taud = (double)tau;
+            rc = TT::implicit_solve(md, th, x, nc, K, a, taud, A.newton_tol, A.newton_maxit,
+                                    A.fd_h, A.jacobian == ML_JAC_ANALYTIC, y);
+            if (rc == 0) {
+#pragma unroll
+              for (int j = 0; j < MM; ++j) {
+                if ((nc >> j) & 1u) {
+                  const double ayj = (double)th[j] * TT::g_real(md, j, y);
+                  const double v = (ayj * taud + (double)K[j]) - (double)a[j] * taud;
+                  const double rv = round(v);
+                  K[j] = rv > 0.0 ? (long long)rv : 0;
+                }
+              }
+            }
+          } else {
+            rc = TT::implicit_solve_fast(md, th, x, nc, K, tau, A.newton_tol,
+                                         A.newton_maxit, A.fd_h,
+                                         A.jacobian == ML_JAC_ANALYTIC);
+          }
           if (rc != 0) {
             status |= ML_ST_NEWTON_FAIL;
             implicit = false;
             tau1 = tau_ex;
             step++;
             continue;
-          }
-#pragma unroll
-          for (int j = 0; j < MM; ++j) {
-            if ((nc >> j) & 1u) {
-              const double ayj = (double)th[j] * TT::g_real(md, j, y);
-              const double v = (ayj * taud + (double)K[j]) - (double)a[j] * taud;
-              const double rv = round(v);
-              K[j] = rv > 0.0 ? (long long)rv : 0;
-            }
           }
         }
         long long xn[NM];
