@@ -127,9 +127,13 @@ POISSON_INV_OPS = 40  # exp, ~3 search steps of 3 ops, uniform
 POISSON_PTRS_OPS = 110
 NEWTON_ITERATIONS = 4.3  # mean iterations per implicit leap on dimerisation states (oracle)
 
-# DRAM bytes per launch measured by ncu for the kernel the default workload runs (see
-# profiles/k_thread_fast_dimerisation_100k.md), keyed by (config, shape)
-PROFILED_TRAFFIC = {(1, 4): 174_592}
+# Per-launch figures measured by ncu for the kernels the default workload runs, keyed by
+# (config, shape): DRAM bytes read + written, warp instructions issued, FP64-pipe busy
+# fraction (profiles/k_thread_fast_dimerisation_100k.md).  Absent: reported as null.
+PROFILED = {
+    (1, 5): {"dram_bytes": 305_408 + 158_976, "warp_inst": 375_367_574, "fp64_pipe_pct": 14.52},
+    (1, 4): {"dram_bytes": 160_512 + 5_120, "warp_inst": 350_663_978, "fp64_pipe_pct": 10.58},
+}
 
 
 def work_model(crn):
@@ -180,6 +184,42 @@ def oracle_rate(w, budget_s, seed=0, first_id=0, jacobian=1):
     return n / dt, n, dt, out
 
 
+def _oracle_worker(task):
+    """One process of the parallel oracle run: trajectory ids [lo, hi) of the workload."""
+    cfg, n_total, lo, hi, seed, jac = task
+    from oracle import oracle as O
+    from paper_1608_07058_gb300 import workloads as W
+    w = W.config(cfg, n_traj=n_total)
+    if hi <= lo:
+        return 0, 0.0
+    xs = w.x0[lo:hi] if w.x0.ndim == 2 else w.x0
+    Ts = w.T[lo:hi] if w.T.size > 1 else w.T
+    th = None if w.theta is None else w.theta[lo:hi]
+    t0 = time.perf_counter()
+    O.simulate(w.crn, hi - lo, xs, Ts, th, params=O.Params(max_steps=MAX_STEPS, jacobian=jac),
+               seed=seed, traj_id_base=lo)
+    return hi - lo, time.perf_counter() - t0
+
+
+def oracle_rate_parallel(cfg, n_total, rate1, budget_s, seed=0, jacobian=1, procs=None):
+    """The unmodified oracle as `procs` independent processes (spawn) over disjoint id
+    ranges, each sized for ~budget_s from the single-core rate; returns (trajectories/s over
+    the wall clock of the timed map, processes, trajectories)."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    per = max(1, int(rate1 * budget_s))
+    per = min(per, max(1, n_total // procs))
+    tasks = [(cfg, n_total, k * per, (k + 1) * per, seed, jacobian) for k in range(procs)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_worker, [(cfg, n_total, 0, 0, seed, jacobian)] * procs)  # start-up
+        t0 = time.perf_counter()
+        done = pool.map(_oracle_worker, tasks)
+        wall = time.perf_counter() - t0
+    n = sum(d[0] for d in done)
+    return n / wall, procs, n
+
+
 def run_reference(args):
     from paper_1608_07058_gb300 import workloads as W
     rank = int(os.environ.get("RANK", "0"))
@@ -194,15 +234,23 @@ def run_reference(args):
         if s >= args.warmup:
             rates.append(rate)
             n_used = n
-    value = statistics.mean(rates)
+    value1 = statistics.mean(rates)
+    # the same oracle on every host core (independent processes over disjoint id ranges)
+    value, procs, n_par = oracle_rate_parallel(args.config, w.n_traj, value1,
+                                               per_step_budget,
+                                               jacobian=1 if args.jacobian == "analytic" else 0)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "trajectories/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * w.n_traj / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(w)},
-            "cpu_baseline": {"value": value, "unit": "trajectories/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {n_used} trajectory ids of the workload per step, "
-                                       f"single-threaded C oracle (FP64 reference algorithm)"},
+            "cpu_baseline": {"value": value, "unit": "trajectories/s", "cores": procs,
+                             "kind": "oracle",
+                             "sample": f"{n_par} trajectories as {procs} independent processes "
+                                       f"over disjoint id ranges of the workload (C oracle, FP64 "
+                                       f"reference algorithm); single-threaded: {value1:.4g} "
+                                       f"trajectories/s on the first {n_used} ids per step"},
+            "cpu_single_core": {"value": value1, "unit": "trajectories/s", "cores": 1},
             "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -472,7 +520,7 @@ def run_ours(args):
     if args.shape:
         fast.shape, fast.block_size = args.shape, args.block
     elif not args.ncu and not args.no_autotune:
-        best = ml.ml_autotune(model, B, x0, T, theta, params=fast, n_sample=min(B, 32768))
+        best = ml.ml_autotune(model, B, x0, T, theta, params=fast, n_sample=min(B, 100_000))
         fast.shape, fast.block_size, fast.ctas_per_sm = best.shape, best.block_size, best.ctas_per_sm
     # the plain form: one launch, each thread runs its trajectory to the end, FP64
     plain = ml.ml_default_params(precision=ml.ML_PREC_REF_FP64, form=ml.ML_FORM_PLAIN,
@@ -497,6 +545,7 @@ def run_ours(args):
         launches = 0
         barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
         t0 = time.perf_counter()
         for k in range(args.steps):
             flush.zero_()
@@ -507,6 +556,7 @@ def run_ours(args):
             launches += ml.ml_model_last_launch_count(model)
             acc += out["counters"].sum(0)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         barrier()
         wall = time.perf_counter() - t0
         ms = [a.elapsed_time(b) for a, b in evs]
@@ -561,13 +611,23 @@ def run_ours(args):
     peak_clock = 2070.0
     peak = sms * 128 * peak_clock * 1e6 / 1e12   # Tops/s: SMs x 4 schedulers x 32 lanes x clock
     achieved = ops_per_launch / (ms_fast / 1e3) / 1e12
-    traffic = PROFILED_TRAFFIC.get((args.config, fast.shape)) if args.n_traj is None else None
+    prof = PROFILED.get((args.config, fast.shape), {}) if args.n_traj is None else {}
+    traffic = prof.get("dram_bytes")
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                         "frac": achieved / peak, "traffic": traffic,
                         "algorithmic_bytes_per_launch": int(B * (8 * model.N + 16 * model.M + 36)
                                                             + (0 if theta is None else B * 8 * model.M)),
                         "peak_basis": f"{sms} SMs x 128 lanes x {peak_clock:.0f} MHz (issue rate, one op per lane per clock)",
                         "work_model_ops_per_event": ops_model}
+    # issue-rate view: warp instructions the kernel issues per launch (ncu) against
+    # SMs x 4 schedulers x one warp instruction per clock
+    inst = prof.get("warp_inst")
+    issue_peak = sms * 4 * peak_clock * 1e6
+    line["roofline"]["issue"] = {
+        "achieved": None if inst is None else inst / (ms_fast / 1e3), "peak": issue_peak,
+        "unit": "warp-inst/s", "frac": None if inst is None else inst / (ms_fast / 1e3) / issue_peak,
+        "warp_inst_per_launch": inst, "fp64_pipe_busy_pct": prof.get("fp64_pipe_pct"),
+        "peak_basis": f"{sms} SMs x 4 warp instructions per clock x {peak_clock:.0f} MHz"}
     if clk:
         line["clocks"] = clk
         line["roofline"]["frac_at_measured_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 / 1e12)
@@ -606,6 +666,13 @@ def run_ours(args):
             line["cpu_baseline"] = {"value": rate, "unit": "trajectories/s", "cores": 1, "kind": "oracle",
                                     "sample": f"first {n} trajectory ids of the workload ({dt:.1f} s), "
                                               f"single-threaded C oracle, FP64 reference algorithm"}
+            prate, procs, pn = oracle_rate_parallel(args.config, w.n_traj, rate,
+                                                    args.cpu_budget_s, seed=res_fast["last_seed"],
+                                                    jacobian=jac)
+            line["cpu_baseline_all_cores"] = {
+                "value": prate, "unit": "trajectories/s", "cores": procs, "kind": "oracle",
+                "sample": f"{pn} trajectories as {procs} independent processes over disjoint id "
+                          f"ranges (spawned pool, start-up excluded)"}
         from tests import stats_util
         g = {k: v[:n].cpu().numpy() for k, v in res_fast["last_out"].items()}
         rows = stats_util.compare(g, oout, g_res=stats_util.G_RESOLUTION_FAST)

@@ -182,7 +182,8 @@ int ml_simulate_host(ml_model* model, int64_t n_traj, const double* theta,
 
 /* Project autotuner: times candidate kernel shapes (trajectory per thread or per warp,
  * threads per CTA, resident CTAs per SM) on the first min(n_traj, n_sample)
- * trajectories of the given inputs, with p's mode/precision/form, and stores the
+ * trajectories of the given inputs, with p's mode/precision/form (one warm-up run, then
+ * the faster of two timed runs per candidate), and stores the
  * fastest in the model (used when a later call passes block_size = 0) and in *best.
  * Synchronizes cuda_stream.  Uses internal scratch outputs. */
 int ml_autotune(ml_model* model, int64_t n_traj, const double* theta, const int64_t* x0,

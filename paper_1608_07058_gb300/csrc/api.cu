@@ -972,24 +972,28 @@ int ml_autotune(ml_model* m, int64_t n_traj, const double* theta, const int64_t*
   float best_ms = 1e30f;
   ml_sim_params best_p = p;
   for (const ml_sim_params& c : cands) {
-    // one warm-up, then one timed run
-    float ms = 0.f;
+    // one warm-up, then the faster of two timed runs
+    float ms = 1e30f;
     bool ok = true;
-    for (int rep = 0; rep < 2 && ok; ++rep) {
-      if (rep == 1) cudaEventRecord(e0, stream);
+    for (int rep = 0; rep < 3 && ok; ++rep) {
+      if (rep > 0) cudaEventRecord(e0, stream);
       int r2 = ml_simulate(m, n, theta, x0, x0_per_traj, T, T_per_traj, &c, seed, 0, X, r, G,
                            stt, cnt, stream);
       if (r2 != ML_OK) ok = false;
-      if (rep == 1) cudaEventRecord(e1, stream);
+      if (rep > 0 && ok) {
+        cudaEventRecord(e1, stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          cudaFree(out);
+          return cuda_fail(cudaGetLastError(), "autotune run");
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (t < ms) ms = t;
+      }
     }
     if (!ok) continue;
-    if (cudaEventSynchronize(e1) != cudaSuccess) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      cudaFree(out);
-      return cuda_fail(cudaGetLastError(), "autotune run");
-    }
-    cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best_ms) {
       best_ms = ms;
       best_p = c;
