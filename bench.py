@@ -679,6 +679,12 @@ def run_ours(args):
         line["parity"] = {"fast_vs_oracle": stats_util.summary(rows), "n_compared": n,
                           "bad_status": res_fast["bad_status"]}
     if rank == 0 and world == 1 and not args.ncu:
+        pk = ml.ml_measure_pipe_peaks()
+        line["pipe_peaks"] = {"fp64_fma_tflops": pk["fp64_fma_flops"] / 1e12,
+                              "fp32_fma_tflops": pk["fp32_fma_flops"] / 1e12,
+                              "mufu_lg2_tops": pk["mufu_lg2_ops"] / 1e12,
+                              "note": "project microbenchmarks (8 independent chains per thread, "
+                                      "8 CTAs of 256 threads per SM, ~20 ms each)"}
         line["bayes_step"] = run_bayes(ml, res_fast["last_out"])
         line["accuracy"] = run_accuracy(ml)
     if rank == 0 and world == 1 and args.serving_seconds > 0 and not args.ncu:

@@ -308,6 +308,14 @@ int ml_kl_divergence(int64_t n_ref, const int64_t* X_ref, int64_t n_test,
                      const int64_t* X_test, int32_t K, int32_t N, int32_t max_bins,
                      double* kl_out, double* kl_mean_out, void* stream);
 
+/* Measurement utility for the roofline (the paper has no counterpart): sustained
+ * throughput of the pipes the simulation kernels use, from project microbenchmarks of
+ * independent dependency chains on every SM of the current device, each run about 20 ms:
+ *   out3[0] FP64 FMA flop/s (an FMA counts 2), out3[1] FP32 FMA flop/s, out3[2]
+ *   special-function (base-2 logarithm) operations/s.
+ * out3: host array of 3 doubles.  Synchronizes stream.  Allocates no device memory. */
+int ml_measure_pipe_peaks(double* out3, void* stream);
+
 /* Number of kernel launches the last ml_simulate/ml_simulate_host call on this model
  * issued (a graph replay counts its kernel nodes), or ML_ERR_ARG. */
 int64_t ml_model_last_launch_count(const ml_model* model);

@@ -43,6 +43,7 @@ def _units():
     u.append(("server.cu", "server.o", []))
     u.append(("bayes.cu", "bayes.o", ["-fmad=false"]))
     u.append(("metrics.cu", "metrics.o", ["-fmad=false"]))
+    u.append(("peaks.cu", "peaks.o", []))
     return u
 
 

@@ -91,6 +91,7 @@ def lib():
                                        v, v, v, v, v, v, v]
         L.ml_kl_divergence.argtypes = [C.c_int64, v, C.c_int64, v, C.c_int32, C.c_int32,
                                        C.c_int32, v, v, v]
+        L.ml_measure_pipe_peaks.argtypes = [P(C.c_double), v]
         L.ml_posterior_sample.argtypes = [C.c_int64, C.c_int32, v, C.c_int32, v, C.c_int32, v, v,
                                           C.c_uint64, C.c_uint64, v, v, v]
         L.ml_resample_workspace_bytes.argtypes = [C.c_int64]
@@ -247,6 +248,14 @@ def ml_kl_divergence(X_ref, X_test, max_bins: int = 1024, kl_out=None, kl_mean=N
                                   K, N, max_bins, _ptr(kl_out), _ptr(kl_mean),
                                   _stream_handle(stream)))
     return kl_out, kl_mean
+
+
+def ml_measure_pipe_peaks(stream=None) -> dict:
+    """Measured FP64 FMA, FP32 FMA (flop/s) and special-function (op/s) throughput of the
+    current device, for the roofline."""
+    out = (C.c_double * 3)()
+    _check(lib().ml_measure_pipe_peaks(out, _stream_handle(stream)))
+    return {"fp64_fma_flops": out[0], "fp32_fma_flops": out[1], "mufu_lg2_ops": out[2]}
 
 
 def ml_simulate_noalloc(model: Model, n_traj: int, x0, T, theta=None,

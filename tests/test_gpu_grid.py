@@ -212,3 +212,4 @@ def test_accuracy_table_dimerisation(ml):
         kl[name] = m.item()
     assert kl["adaptive"] > 3 * kl["ssa"], kl
     assert kl["explicit"] < kl["adaptive"], kl
+
