@@ -7,12 +7,16 @@ T = 0.2, eps = 0.03, n_c = 10, 100,000 trajectories per GPU (weak scaling: rank 
 trajectory ids [k B, (k+1) B)).
 
 A step is one simulate call over the whole batch.  Two forms are timed:
-  batched  fast precision (FP32 propensities, FP64 t/G/Newton), persistent refill
-           kernel launched from a CUDA graph, autotuned shape  -> the headline `value`;
+  batched  fast precision (FP32 propensities, step sizes, Poisson means and implicit
+           Newton solve; FP64 time and G totals), persistent refill kernel launched from
+           a CUDA graph, autotuned shape  -> the headline `value`;
   plain    reference precision (FP64 everywhere), one launch, one thread per trajectory.
 Inputs are resident in HBM when timing starts; a 256 MB buffer is written between steps to
 flush L2.  `e2e` times the host-buffer entry point (pinned host memory, copies inside).
-`cpu_baseline` times the CPU oracle on the host, single-threaded, on a bounded sample.
+`cpu_baseline` times the CPU oracle on one host core on a bounded sample and
+`cpu_baseline_all_cores` as one process per core; `roofline` reports the algorithmic and
+the issue-rate view, `pipe_peaks` the measured pipe throughputs, `bayes_step` the
+posterior draw and resampling, `accuracy` the paper's KL study (Section 3, Table 1).
 `--impl reference` times only the oracle (the reference arm for this method).
 """
 import argparse
