@@ -276,15 +276,7 @@ mlk::KernelEntry warp_grid_entry(int precision) {
   return precision == ML_PREC_FAST_FP32 ? mlk::warp_grid_entry_fast() : mlk::warp_grid_entry_ref();
 }
 
-bool is_device_pointer(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
+using mlk::is_device_pointer;
 
 int check_params(const ml_sim_params& p) {
   if (!(p.eps > 0.0 && p.eps < 1.0)) return fail(ML_ERR_ARG, "eps must be in (0, 1)");
@@ -559,6 +551,16 @@ int check_sizes(const ml_model* m, int64_t n_traj, uint64_t id_base) {
 namespace mlk {
 
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+bool is_device_pointer(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
 
 int noalloc_prepare(const ml_model* m, int64_t n_traj, const double* theta, const int64_t* x0,
                     int32_t x0_per_traj, const double* T, int32_t T_per_traj,

@@ -198,16 +198,6 @@ __global__ void k_ancestors(int64_t n, const uint64_t* __restrict__ incl,
   anc[k] = lo;
 }
 
-bool device_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
 size_t resample_ws(int64_t n) {
   const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
   return 256 + (size_t)n * 8 + (size_t)nb * 8 + 256;
@@ -229,8 +219,8 @@ int ml_posterior_sample(int64_t n, int32_t M, const double* alpha, int32_t alpha
   if (n == 0) return ML_OK;
   const void* req[] = {alpha, beta, r, G, theta_out};
   for (const void* p : req)
-    if (!device_ptr(p)) return set_error(ML_ERR_ARG, "alpha, beta, r, G and theta_out must be device memory");
-  if (status_out && !device_ptr(status_out)) return set_error(ML_ERR_ARG, "status_out must be device memory");
+    if (!is_device_pointer(p)) return set_error(ML_ERR_ARG, "alpha, beta, r, G and theta_out must be device memory");
+  if (status_out && !is_device_pointer(status_out)) return set_error(ML_ERR_ARG, "status_out must be device memory");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (status_out) {
     cudaError_t e = cudaMemsetAsync(status_out, 0, (size_t)n * 4, s);
@@ -254,7 +244,7 @@ int ml_resample_systematic(int64_t n, const double* logw, uint64_t seed, uint64_
   using namespace mlk;
   // q_i <= 2^40, so the 64-bit prefix sums stay exact for n < 2^24.
   if (n < 1 || n >= (1LL << 24)) return set_error(ML_ERR_ARG, "need 1 <= n < 2^24");
-  if (!device_ptr(logw) || !device_ptr(ancestors) || !device_ptr(workspace))
+  if (!is_device_pointer(logw) || !is_device_pointer(ancestors) || !is_device_pointer(workspace))
     return set_error(ML_ERR_ARG, "logw, ancestors and workspace must be device memory");
   if (workspace_bytes < resample_ws(n))
     return set_error(ML_ERR_ARG, "workspace smaller than ml_resample_workspace_bytes(n)");

@@ -118,16 +118,6 @@ __global__ void k_kl_mean(int n, const double* __restrict__ kl, double* __restri
   if (threadIdx.x == 0) *mean = s / (double)n;
 }
 
-bool device_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 }  // namespace mlk
 
@@ -141,9 +131,9 @@ extern "C" int ml_kl_divergence(int64_t n_ref, const int64_t* X_ref, int64_t n_t
     return set_error(ML_ERR_ARG, "need K >= 1, N >= 1 and K * N < 2^31");
   if (max_bins < 1 || max_bins > kKlMaxBins)
     return set_error(ML_ERR_ARG, "need 1 <= max_bins <= 4096");
-  if (!device_ptr(X_ref) || !device_ptr(X_test) || !device_ptr(kl_out))
+  if (!is_device_pointer(X_ref) || !is_device_pointer(X_test) || !is_device_pointer(kl_out))
     return set_error(ML_ERR_ARG, "X_ref, X_test and kl_out must be device memory");
-  if (kl_mean_out && !device_ptr(kl_mean_out))
+  if (kl_mean_out && !is_device_pointer(kl_mean_out))
     return set_error(ML_ERR_ARG, "kl_mean_out must be device memory");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_kl<<<(unsigned)(K * N), kKlThreads, 0, s>>>(n_ref, X_ref, n_test, X_test, K, N, max_bins,

@@ -186,5 +186,7 @@ int noalloc_prepare(const ml_model* m, int64_t n_traj, const double* theta, cons
                     int64_t* r, double* G, uint32_t* status, int64_t* counters,
                     size_t scratch_table_max, NoAllocLaunch* out);
 int set_error(int code, const char* msg);
+// True for device or managed memory (a failed query clears the CUDA error and is false).
+bool is_device_pointer(const void* p);
 
 }  // namespace mlk
