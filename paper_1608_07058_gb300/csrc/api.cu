@@ -105,7 +105,7 @@ std::vector<uint8_t> build_thread_tables(const ml_model& m) {
       t.nu[j][s] = in ? (int8_t)m.nu[j * m.N + s] : 0;
     }
   }
-  for (int j = 0; j < m.M; ++j)
+  for (int j = 0; j < m.M && j < MM; ++j)  // the variant always holds the model (M <= MM)
     if (m.partner[j] > j) t.partner[j] = (int8_t)m.partner[j];
   for (int s = 0; s < NM; ++s) {
     t.isreact[s] = s < m.N ? m.isreact[s] : 0;
@@ -493,8 +493,7 @@ int launch_graph(DeviceState& st, const ml_sim_params& p, const Plan& plan,
   GraphCache& gc = st.graphs[{p.precision, key2}];
   const void* tables = plan.tables;
   void* kargs[2] = {const_cast<void**>(&tables), &a};
-  cudaKernelNodeParams kp;
-  std::memset(&kp, 0, sizeof kp);
+  cudaKernelNodeParams kp{};
   kp.func = const_cast<void*>(plan.entry.kernel);
   kp.gridDim = dim3((unsigned)plan.grid);
   kp.blockDim = dim3((unsigned)plan.block);
