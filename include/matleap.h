@@ -90,7 +90,9 @@ extern "C" {
                                      in the occupancy build                           */
 
 /* ---- Jacobian of the implicit solve (Section 1: estimated numerically, or the
- *      symbolic Jacobian of Section 3) ------------------------------------------------- */
+ *      symbolic Jacobian of Section 3).  Reference precision and the warp kernel follow
+ *      the choice; the fast-precision thread kernel always uses the exact derivative
+ *      (there the Jacobian only sets the convergence rate, not the solution). -------- */
 #define ML_JAC_FD 0       /* forward differences                                          */
 #define ML_JAC_ANALYTIC 1 /* exact derivative of the mass-action polynomials              */
 

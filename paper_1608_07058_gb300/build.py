@@ -26,16 +26,28 @@ def _nvcc():
     raise RuntimeError("nvcc not found: the CUDA library cannot be built")
 
 
+# The generic thread variant (8 species x 16 reactions) is large: its kernels are
+# compiled as separate units (ML_PART) so that they build in parallel.
+SPLIT_VARIANTS = (N_THREAD_VARIANTS - 1,)
+
+
+def _thread_units(name, flags, v, parts):
+    if v not in SPLIT_VARIANTS:
+        return [("kern_thread.cu", f"kt_{name}_{v}.o", flags)]
+    return [("kern_thread.cu", f"kt_{name}_{v}_p{k}.o", flags + [f"-DML_PART={k}"])
+            for k in parts]
+
+
 def _units():
     u = []
     for fast in (0, 1):
         for v in range(N_THREAD_VARIANTS):
-            u.append(("kern_thread.cu", f"kt_{'fast' if fast else 'ref'}_{v}.o",
-                      [f"-DML_FAST={fast}", f"-DML_VARIANT={v}"] + ([] if fast else ["-fmad=false"])))
+            u += _thread_units("fast" if fast else "ref", [f"-DML_FAST={fast}", f"-DML_VARIANT={v}"]
+                               + ([] if fast else ["-fmad=false"]), v, (0, 1, 2))
         if fast:
             for v in range(N_THREAD_VARIANTS):
-                u.append(("kern_thread.cu", f"kt_fastocc_{v}.o",
-                          ["-DML_FAST=1", f"-DML_VARIANT={v}", "-DML_THREAD_MIN_BLOCKS=2"]))
+                u += _thread_units("fastocc", ["-DML_FAST=1", f"-DML_VARIANT={v}",
+                                               "-DML_THREAD_MIN_BLOCKS=2"], v, (0, 1))
         u.append(("kern_warp.cu", f"kw_{'fast' if fast else 'ref'}.o",
                   [f"-DML_FAST={fast}"] + ([] if fast else ["-fmad=false"])))
     u.append(("api.cu", "api.o", []))
@@ -71,6 +83,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         jobs.append(cmd)
+    # the generic variant's units take longest: start them first
+    heavy = [f"-DML_VARIANT={v}" for v in SPLIT_VARIANTS]
+    jobs.sort(key=lambda c: 0 if any(h in c for h in heavy) else 1)
     with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
         results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
     for cmd, res in zip(jobs, results):

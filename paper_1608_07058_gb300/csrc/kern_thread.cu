@@ -5,7 +5,15 @@
 //   CTA, about 168 registers, more resident warps, some spilling), offered to the
 //   autotuner as a separate shape.  The plain builds also carry the sequential driver
 //   with time-grid output.
+//   ML_PART (optional): build only the round-based driver (0), the sequential driver (1)
+//   or its time-grid build (2) of this variant, so that the large generic variant's
+//   kernels compile in parallel units; unset, the unit holds all of them.
 #include "thread_core.cuh"
+
+#ifndef ML_PART
+#define ML_PART -1
+#endif
+#define ML_HAS_PART(k) (ML_PART < 0 || ML_PART == (k))
 
 #ifndef ML_VARIANT
 #error "ML_VARIANT must be defined"
@@ -28,19 +36,23 @@ using Prec = PrecRef;
 namespace {
 constexpr int kNM = kThreadN[ML_VARIANT];
 constexpr int kMM = kThreadM[ML_VARIANT];
+#if ML_HAS_PART(0)
 cudaError_t launch(const void* dm, const SimArgs& a, int grid, int block, size_t smem,
                    cudaStream_t s) {
   k_thread<kNM, kMM, Prec><<<grid, block, smem, s>>>(
       static_cast<const ThreadModel<kNM, kMM>*>(dm), a);
   return cudaGetLastError();
 }
+#endif
+#if ML_HAS_PART(1)
 cudaError_t launch_seq(const void* dm, const SimArgs& a, int grid, int block, size_t smem,
                        cudaStream_t s) {
   k_thread_seq<kNM, kMM, Prec><<<grid, block, smem, s>>>(
       static_cast<const ThreadModel<kNM, kMM>*>(dm), a);
   return cudaGetLastError();
 }
-#if !(ML_FAST && ML_THREAD_MIN_BLOCKS == 2)
+#endif
+#if !(ML_FAST && ML_THREAD_MIN_BLOCKS == 2) && ML_HAS_PART(2)
 cudaError_t launch_seq_grid(const void* dm, const SimArgs& a, int grid, int block, size_t smem,
                             cudaStream_t s) {
   k_thread_seq<kNM, kMM, Prec, true><<<grid, block, smem, s>>>(
@@ -50,16 +62,20 @@ cudaError_t launch_seq_grid(const void* dm, const SimArgs& a, int grid, int bloc
 #endif
 }  // namespace
 
-#if !(ML_FAST && ML_THREAD_MIN_BLOCKS == 2)
+#if !(ML_FAST && ML_THREAD_MIN_BLOCKS == 2) && ML_HAS_PART(2)
 KernelEntry ML_CAT(thread_seq_grid_entry_, ML_PNAME, ML_VARIANT)() {
   return KernelEntry{&launch_seq_grid,
                      reinterpret_cast<const void*>(&k_thread_seq<kNM, kMM, Prec, true>)};
 }
 #endif
+#if ML_HAS_PART(0)
 KernelEntry ML_CAT(thread_entry_, ML_PNAME, ML_VARIANT)() {
   return KernelEntry{&launch, reinterpret_cast<const void*>(&k_thread<kNM, kMM, Prec>)};
 }
+#endif
+#if ML_HAS_PART(1)
 KernelEntry ML_CAT(thread_seq_entry_, ML_PNAME, ML_VARIANT)() {
   return KernelEntry{&launch_seq, reinterpret_cast<const void*>(&k_thread_seq<kNM, kMM, Prec>)};
 }
+#endif
 }  // namespace mlk

@@ -499,13 +499,14 @@ struct ThreadTraj {
   // counts K_j = P_j + round(tau theta_j (g_j(x + z) - g_j(x))) within rounding of the
   // FP64 solution (on dimerisation states one leap in about 200 differs by one firing,
   // with no preferred sign).  The stopping test uses max(tol, 1e-6) (FP32 cannot resolve
-  // 1e-10), and a forward-difference step of at least 2^-11 relative.  On success K holds
-  // the counts.  Returns 0 converged, 1 not converged, 2 singular.
+  // 1e-10).  On success K holds the counts.  The Jacobian is always the exact one (the paper's symbolic Jacobian): in
+  // this FP32 solve it only sets the rate of convergence, the exact derivative is the
+  // cheaper to evaluate, and leaving out the forward-difference variant keeps the
+  // generic 8 x 16 build compact.  Returns 0 converged, 1 not converged, 2 singular.
   __device__ static __forceinline__ int implicit_solve_fast(const Model& md, const R (&th)[MM],
                                             const long long (&x)[NM], uint32_t nc,
                                             long long (&K)[MM], R tau,
-                                            double tol, int maxit, double fd_h,
-                                            bool analytic) {
+                                            double tol, int maxit) {
     R xf[NM], z[NM], c[NM];
 #pragma unroll
     for (int s = 0; s < NM; ++s) {
@@ -518,7 +519,6 @@ struct ThreadTraj {
       c[s] = (R)cs;
     }
     const R tolr = tol > 1e-6 ? (R)tol : R(1e-6);
-    const R hrel = fd_h > 0x1p-11 ? (R)fd_h : R(0x1p-11);
     for (int it = 0; it < maxit; ++it) {
       R dg[MM];
 #pragma unroll
@@ -538,25 +538,11 @@ struct ThreadTraj {
 #pragma unroll
       for (int q = 0; q < NM; ++q) {
         R Dq[MM];
-        if (analytic) {
 #pragma unroll
-          for (int j = 0; j < MM; ++j)
-            Dq[j] = (((nc >> j) & 1u) && md.ord[j][q] != 0)
-                        ? th[j] * g_real_deriv<R>(md, j, yr, q)
-                        : R(0);
-        } else {
-          const R aq = fabs(yr[q]);
-          R zq[NM];
-#pragma unroll
-          for (int s = 0; s < NM; ++s) zq[s] = z[s];
-          zq[q] = z[q] + hrel * (aq > R(1) ? aq : R(1));
-          const R he = zq[q] - z[q];
-#pragma unroll
-          for (int j = 0; j < MM; ++j)
-            Dq[j] = (((nc >> j) & 1u) && md.ord[j][q] != 0)
-                        ? th[j] * ((g_diff(md, j, xf, zq) - dg[j]) / he)
-                        : R(0);
-        }
+        for (int j = 0; j < MM; ++j)
+          Dq[j] = (((nc >> j) & 1u) && md.ord[j][q] != 0)
+                      ? th[j] * g_real_deriv<R>(md, j, yr, q)
+                      : R(0);
 #pragma unroll
         for (int s = 0; s < NM; ++s) {
           R acc = R(0);
@@ -1036,8 +1022,7 @@ struct ThreadLane {
             }
           } else {
             rc = TT::implicit_solve_fast(md, th, x, nc, K, tau, A.newton_tol,
-                                         A.newton_maxit, A.fd_h,
-                                         A.jacobian == ML_JAC_ANALYTIC);
+                                         A.newton_maxit);
           }
           if (rc != 0) {
             status |= ML_ST_NEWTON_FAIL;
