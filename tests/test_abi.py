@@ -144,3 +144,25 @@ def test_bayes_argument_errors_without_device(ml):
     p = a.ctypes.data
     assert L.ml_posterior_sample(4, 3, p, 0, p, 0, p, p, 0, 0, p, None, None) == ml.ML_ERR_ARG
     assert "device memory" in ml.ml_last_error()
+
+
+def test_grid_kl_and_peaks_argument_errors_without_device(ml):
+    """The time-grid, KL and pipe-peak entry points reject malformed arguments on the host
+    before touching a device."""
+    import ctypes as C
+    L = ml.lib()
+    m = ml.model_from_crn(W.config(0, n_traj=1).crn)
+    p = ml.ml_default_params()
+    args = lambda K, tobs, xobs: (C.c_void_p(m.handle), 4, None, None, 0, None, 0, C.byref(p),
+                                  0, 0, tobs, K, xobs, None, None, None, None, None, None)
+    assert L.ml_simulate_grid(*args(-1, None, None)) == ml.ML_ERR_ARG
+    assert L.ml_simulate_grid(*args(3, None, None)) == ml.ML_ERR_ARG      # K > 0, no grid
+    host = np.zeros(8)
+    assert L.ml_simulate_grid(*args(3, host.ctypes.data, host.ctypes.data)) == ml.ML_ERR_ARG
+    assert "device memory" in ml.ml_last_error()
+    kl = lambda n1, n2, K, N, b: L.ml_kl_divergence(n1, None, n2, None, K, N, b, None, None, None)
+    assert kl(0, 5, 1, 1, 16) == ml.ML_ERR_ARG
+    assert kl(5, 5, 0, 1, 16) == ml.ML_ERR_ARG
+    assert kl(5, 5, 1, 1, 0) == ml.ML_ERR_ARG and kl(5, 5, 1, 1, 4097) == ml.ML_ERR_ARG
+    assert kl(5, 5, 1, 1, 16) == ml.ML_ERR_ARG                          # NULL buffers
+    assert L.ml_measure_pipe_peaks(None, None) == ml.ML_ERR_ARG
