@@ -129,3 +129,38 @@ def test_parsed_model_goes_to_the_library():
     model = matleap.model_from_crn(m.crn)
     assert matleap.ml_model_num_pairs(model) == 1
     assert model.N == 3 and model.M == 4
+
+
+def test_round_trip_random_networks():
+    """Any mass-action network (orders up to 3, products up to 3 per species, rates over
+    many decades, zero-order sources) survives write_sbml -> read_sbml exactly."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=60, deadline=None)
+    @hyp.given(st.data())
+    def check(data):
+        N = data.draw(st.integers(1, 6))
+        M = data.draw(st.integers(1, 8))
+        reactions = []
+        for _ in range(M):
+            re, pr, total = {}, {}, 0
+            for s in range(N):
+                m = data.draw(st.integers(0, 3 - total))
+                if m:
+                    re[s] = m
+                    total += m
+                q = data.draw(st.integers(0, 3))
+                if q:
+                    pr[s] = q
+            k = data.draw(st.floats(1e-12, 1e12, allow_nan=False, allow_infinity=False))
+            reactions.append((re, pr, k))
+        crn = W._crn("random", N, reactions, tuple(f"X{s}" for s in range(N)))
+        x0 = data.draw(st.lists(st.integers(0, 10**12), min_size=N, max_size=N))
+        m = sbml.read_sbml(sbml.write_sbml(crn, x0))
+        assert np.array_equal(m.crn.orders, crn.orders)
+        assert np.array_equal(m.crn.stoich, crn.stoich)
+        assert np.array_equal(m.crn.rates, crn.rates)
+        assert np.array_equal(m.x0, np.asarray(x0, np.int64))
+
+    check()
