@@ -122,7 +122,8 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------
-# algorithmic work model (arithmetic the method needs per event)
+# algorithmic work model: the arithmetic the method needs per event (explicit leap,
+# implicit leap with its Newton iterations, SSA firing, rejected leap)
 # ---------------------------------------------------------------------------------
 PHILOX_OPS = 70      # 10 rounds x (2 wide multiplies, 3 xors, 2 key adds)
 UNIFORM_OPS = 3
