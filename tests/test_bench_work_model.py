@@ -1,5 +1,6 @@
 """The benchmark's algorithmic work model (operations per event, the numerator of the
-`alu` roofline) gives the figures DESIGN quotes for the dimerisation, and on the
+`alu` roofline) gives explicit leap 538, implicit leap 1,049.6 (4.3 Newton iterations), SSA firing
+126.5 and rejected leap 520 operations for the dimerisation, and on the
 single-reaction pure-decay network the counts a hand tally gives: propensity 2 (one
 factor, one rate product), SSA firing 2 + 70 (Philox) + 6 (two uniforms) + 15 (log) + 1 +
 2 + 2 + 2 + 1 = 101, explicit leap 132, one Newton iteration 19, implicit leap
