@@ -604,6 +604,113 @@ int mlo_implicit_solve(int32_t N, int32_t M, const int32_t* orders, const int32_
 }
 
 /* ------------------------------------------------------------------------------------
+ * The decisions of one outer step (Section 2), one function each.  The trajectory loop
+ * below calls exactly these, and they are exported so that tests pin each one on
+ * hand-computed states.
+ * ---------------------------------------------------------------------------------- */
+
+/* Critical reactions (Section 2: a reaction fewer than n_c firings away from exhausting
+ * one of its reactants fires at most once per leap).  L_j = min over the species that
+ * reaction j consumes (nu_js < 0; a catalyst, with nu_js = 0, is not consumed) of
+ * floor(x_s / |nu_js|); j is critical iff a_j > 0 and L_j < n_c (a reaction that
+ * consumes nothing is never critical).  crit[j] = 1 for a critical reaction, else 0;
+ * ac[j] = a_j for a critical reaction, else 0.  Returns a0c, the lane-tree sum of ac. */
+static double critical_set_md(const model_t* md, const double* a, const int64_t* x,
+                              int32_t n_c, uint8_t* crit, double* ac) {
+  const int32_t N = md->N, M = md->M;
+  for (int32_t j = 0; j < M; ++j) {
+    int c = 0;
+    if (a[j] > 0.0) {
+      int64_t L = -1;
+      for (int32_t s = 0; s < N; ++s) {
+        int32_t v = md->nu[j * N + s];
+        if (v >= 0) continue;
+        int64_t l = x[s] / (int64_t)(-v);
+        if (L < 0 || l < L) L = l;
+      }
+      c = (L >= 0 && L < (int64_t)n_c);
+    }
+    crit[j] = (uint8_t)c;
+    ac[j] = c ? a[j] : 0.0;
+  }
+  return mlo_lane_tree_sum(ac, M);
+}
+
+double mlo_critical_set(int32_t N, int32_t M, const int32_t* orders, const int32_t* stoich,
+                        const double* a, const int64_t* x, int32_t n_c, uint8_t* crit_out,
+                        double* ac_out) {
+  model_t md;
+  if (model_init(&md, N, M, orders, stoich) != 0) {
+    model_free(&md);
+    return NAN;
+  }
+  double a0c = critical_set_md(&md, a, x, n_c, crit_out, ac_out);
+  model_free(&md);
+  return a0c;
+}
+
+/* Inverse-CDF choice of one reaction (Gillespie 1977 direct method; also the critical
+ * pick): the first j, in index order, whose sequential prefix sum w_0 + ... + w_j exceeds
+ * target; when rounding leaves none, the last j with w_j > 0; -1 when no weight is
+ * positive. */
+int32_t mlo_pick(int32_t M, const double* w, double target) {
+  double acc = 0.0;
+  int32_t last = -1;
+  for (int32_t j = 0; j < M; ++j) {
+    if (w[j] > 0.0) last = j;
+    acc = acc + w[j];
+    if (target < acc) return j;
+  }
+  return last;
+}
+
+/* The paper's switch to exact SSA (Section 2), folded with Cao's rule that a leap of
+ * fewer than ssa_factor mean inter-reaction waits is not worth taking: 1 iff
+ * min(tau1, tau2) < ssa_factor / a0, where tau2 is the drawn wait to the next critical
+ * firing (+inf without critical reactions). */
+int mlo_ssa_switch(double tau1, double tau2, double a0, double ssa_factor) {
+  double tmin = tau1 < tau2 ? tau1 : tau2;
+  return tmin < ssa_factor / a0;
+}
+
+/* Firings of one non-critical reaction in an implicit leap (Rathinam 2003): the real
+ * solution y gives a_j(y) tau + P_j - a_j(x) tau, rounded half away from zero and clamped
+ * at 0 (this project's reading: the clamp keeps r >= 0 and X = x0 + nu^T r exact). */
+int64_t mlo_implicit_count(double a_y, double tau, double P, double a_x) {
+  double v = (a_y * tau + P) - a_x * tau;
+  double rv = round(v);
+  return rv > 0.0 ? (int64_t)rv : 0;
+}
+
+/* One implicit leap: solve for y (implicit_solve_md), then K[j] = mlo_implicit_count for
+ * every non-critical j (K of critical reactions untouched).  Returns the solve's code. */
+static int implicit_leap_md(const model_t* md, const double* th, const int64_t* x,
+                            const uint8_t* nc, const double* P, const double* a_x, double tau,
+                            const mlo_params* p, double* y, int64_t* K, int32_t* iters) {
+  int rc = implicit_solve_md(md, th, x, nc, P, a_x, tau, p, y, iters);
+  if (rc != 0) return rc;
+  for (int32_t j = 0; j < md->M; ++j)
+    if (nc[j]) K[j] = mlo_implicit_count(th[j] * g_real(md, j, y), tau, P[j], a_x[j]);
+  return 0;
+}
+
+int mlo_implicit_leap(int32_t N, int32_t M, const int32_t* orders, const int32_t* stoich,
+                      const double* theta, const int64_t* x, const uint8_t* nc,
+                      const double* P, const double* a_x, double tau, const mlo_params* p,
+                      int64_t* K_out, int32_t* iters_out) {
+  model_t md;
+  if (model_init(&md, N, M, orders, stoich) != 0) {
+    model_free(&md);
+    return -1;
+  }
+  double* y = (double*)malloc(sizeof(double) * (size_t)N);
+  int rc = implicit_leap_md(&md, theta, x, nc, P, a_x, tau, p, y, K_out, iters_out);
+  free(y);
+  model_free(&md);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------------------
  * Parameters
  * ---------------------------------------------------------------------------------- */
 void mlo_default_params(mlo_params* p) {
@@ -710,17 +817,7 @@ static void ssa_burst(traj_t* tr, uint32_t step, int32_t n_max, double a0) {
     for (int32_t j = 0; j < M; ++j) tr->G[j] = tr->G[j] + tr->g[j] * dt;
     record_obs(tr, tn, 0); /* grid points before the firing see the old state */
     tr->t = tn;
-    double target = u2 * a0, acc = 0.0;
-    int32_t pick = -1, last = -1;
-    for (int32_t j = 0; j < M; ++j) {
-      if (tr->a[j] > 0.0) last = j;
-      acc = acc + tr->a[j];
-      if (target < acc) {
-        pick = j;
-        break;
-      }
-    }
-    if (pick < 0) pick = last;
+    int32_t pick = mlo_pick(M, tr->a, u2 * a0);
     for (int32_t s = 0; s < N; ++s) tr->x[s] += md->nu[pick * N + s];
     tr->r[pick] += 1;
     tr->cnt[2] += 1;
@@ -737,6 +834,7 @@ static void simulate_one(traj_t* tr) {
   double* Pd = (double*)malloc(sizeof(double) * (size_t)M);
   double* y = (double*)malloc(sizeof(double) * (size_t)N);
   uint8_t* nc = (uint8_t*)malloc((size_t)M);
+  uint8_t* crit = (uint8_t*)malloc((size_t)M);
   uint8_t* use_im = (uint8_t*)malloc((size_t)M);
   uint8_t* pe_on = (uint8_t*)malloc((size_t)M);
   int64_t* K = (int64_t*)malloc(sizeof(int64_t) * (size_t)M);
@@ -765,24 +863,9 @@ static void simulate_one(traj_t* tr) {
       step++;
       continue;
     }
-    /* 2. critical reactions: a_j > 0 and L_j = min over consumed s of floor(x_s/|nu_js|)
-     *    below n_c */
-    for (int32_t j = 0; j < M; ++j) {
-      int crit = 0;
-      if (tr->a[j] > 0.0) {
-        int64_t L = -1;
-        for (int32_t s = 0; s < N; ++s) {
-          int32_t v = md->nu[j * N + s];
-          if (v >= 0) continue;
-          int64_t l = tr->x[s] / (int64_t)(-v);
-          if (L < 0 || l < L) L = l;
-        }
-        crit = (L >= 0 && L < (int64_t)p->n_c);
-      }
-      nc[j] = (uint8_t)!crit;
-      ac[j] = crit ? tr->a[j] : 0.0;
-    }
-    double a0c = mlo_lane_tree_sum(ac, M);
+    /* 2. critical reactions and a0c */
+    double a0c = critical_set_md(md, tr->a, tr->x, p->n_c, crit, ac);
+    for (int32_t j = 0; j < M; ++j) nc[j] = (uint8_t)!crit[j];
     /* 3. explicit step size */
     double tau_ex = tau_select_md(md, tr->a, tr->x, nc, p->eps);
     /* 4. partial equilibrium and the implicit step size */
@@ -824,8 +907,7 @@ static void simulate_one(traj_t* tr) {
         block_words(tr->seed, tr->id, step, (uint32_t)M, 0u, w);
         tau2 = -mlo_log(mlo_u01_from_words(w[0], w[1])) / a0c;
       }
-      double tmin = tau1 < tau2 ? tau1 : tau2;
-      if (tmin < p->ssa_factor / a0) {
+      if (mlo_ssa_switch(tau1, tau2, a0, p->ssa_factor)) {
         ssa_burst(tr, step, implicit ? p->n_ssa_implicit : p->n_ssa_explicit, a0);
         step++;
         reject_run = 0;
@@ -845,18 +927,7 @@ static void simulate_one(traj_t* tr) {
       if (crit_fire) {
         uint32_t w[4];
         block_words(tr->seed, tr->id, step, (uint32_t)M + 1u, 0u, w);
-        double target = mlo_u01_from_words(w[0], w[1]) * a0c, acc = 0.0;
-        int32_t pick = -1, last = -1;
-        for (int32_t j = 0; j < M; ++j) {
-          if (ac[j] > 0.0) last = j;
-          acc = acc + ac[j];
-          if (target < acc) {
-            pick = j;
-            break;
-          }
-        }
-        if (pick < 0) pick = last;
-        K[pick] = 1;
+        K[mlo_pick(M, ac, mlo_u01_from_words(w[0], w[1]) * a0c)] = 1;
       }
       int implicit_step = implicit && tau > tau_ex;
       if (implicit_step) {
@@ -865,20 +936,12 @@ static void simulate_one(traj_t* tr) {
                                               (uint32_t)j, &tr->status)
                         : 0.0;
         int32_t its;
-        int rc = implicit_solve_md(md, tr->th, tr->x, nc, Pd, tr->a, tau, p, y, &its);
-        if (rc != 0) {
+        if (implicit_leap_md(md, tr->th, tr->x, nc, Pd, tr->a, tau, p, y, K, &its) != 0) {
           tr->status |= MLO_ST_NEWTON_FAIL;
           implicit = 0;
           tau1 = tau_ex;
           step++;
           continue;
-        }
-        for (int32_t j = 0; j < M; ++j) {
-          if (!nc[j]) continue;
-          double ayj = tr->th[j] * g_real(md, j, y);
-          double v = (ayj * tau + Pd[j]) - tr->a[j] * tau;
-          double rv = round(v);
-          K[j] = rv > 0.0 ? (int64_t)rv : 0;
         }
       } else {
         for (int32_t j = 0; j < M; ++j)
@@ -917,7 +980,7 @@ static void simulate_one(traj_t* tr) {
   }
   /* grid points after the end (beyond T, or after a step-limit stop) see the final state */
   record_obs(tr, INFINITY, 1);
-  free(ac); free(gn); free(Pd); free(y); free(nc); free(use_im); free(pe_on);
+  free(ac); free(gn); free(Pd); free(y); free(nc); free(crit); free(use_im); free(pe_on);
   free(K); free(xn);
 }
 

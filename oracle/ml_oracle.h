@@ -113,6 +113,25 @@ void mlo_poisson_batch(double mu, uint64_t seed, int64_t n, int64_t* out);
 /* Cao 2006 step size for one state (all reactions non-critical unless crit_mask set). */
 double mlo_tau_select(int32_t N, int32_t M, const int32_t* orders, const int32_t* stoich,
                       const double* a, const int64_t* x, const uint8_t* use, double eps);
+/* Critical reactions: crit_out[j] = 1 iff a_j > 0 and L_j = min over species consumed by
+ * j (nu_js < 0) of floor(x_s / |nu_js|) is below n_c; ac_out[j] = a_j for critical j,
+ * else 0.  Returns a0c (lane-tree sum of ac_out), NaN for a malformed model. */
+double mlo_critical_set(int32_t N, int32_t M, const int32_t* orders, const int32_t* stoich,
+                        const double* a, const int64_t* x, int32_t n_c, uint8_t* crit_out,
+                        double* ac_out);
+/* Inverse-CDF pick: first j whose sequential prefix sum of w exceeds target, else the
+ * last j with w_j > 0, else -1. */
+int32_t mlo_pick(int32_t M, const double* w, double target);
+/* The SSA switch: 1 iff min(tau1, tau2) < ssa_factor / a0. */
+int mlo_ssa_switch(double tau1, double tau2, double a0, double ssa_factor);
+/* Implicit firing count max(0, round((a_y tau + P) - a_x tau)), half away from zero. */
+int64_t mlo_implicit_count(double a_y, double tau, double P, double a_x);
+/* Implicit solve followed by mlo_implicit_count for every j with nc[j] (K_out of the
+ * others untouched).  Returns the solve's code (0 converged, 1 not, 2 singular). */
+int mlo_implicit_leap(int32_t N, int32_t M, const int32_t* orders, const int32_t* stoich,
+                      const double* theta, const int64_t* x, const uint8_t* nc,
+                      const double* P, const double* a_x, double tau, const mlo_params* p,
+                      int64_t* K_out, int32_t* iters_out);
 /* Canonical lane-tree sum (used for a0 and a0c). */
 double mlo_lane_tree_sum(const double* v, int32_t n);
 /* One implicit solve (Rathinam 2003): returns 0 on convergence and writes y, iterations. */

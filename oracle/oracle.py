@@ -89,6 +89,21 @@ def lib(extra_flags=()):
         L.mlo_tau_select.argtypes = [C.c_int32, C.c_int32, P(C.c_int32), P(C.c_int32),
                                      P(C.c_double), P(C.c_int64), P(C.c_uint8), C.c_double]
         L.mlo_tau_select.restype = C.c_double
+        L.mlo_critical_set.argtypes = [C.c_int32, C.c_int32, P(C.c_int32), P(C.c_int32),
+                                       P(C.c_double), P(C.c_int64), C.c_int32, P(C.c_uint8),
+                                       P(C.c_double)]
+        L.mlo_critical_set.restype = C.c_double
+        L.mlo_pick.argtypes = [C.c_int32, P(C.c_double), C.c_double]
+        L.mlo_pick.restype = C.c_int32
+        L.mlo_ssa_switch.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
+        L.mlo_ssa_switch.restype = C.c_int
+        L.mlo_implicit_count.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
+        L.mlo_implicit_count.restype = C.c_int64
+        L.mlo_implicit_leap.argtypes = [C.c_int32, C.c_int32, P(C.c_int32), P(C.c_int32),
+                                        P(C.c_double), P(C.c_int64), P(C.c_uint8),
+                                        P(C.c_double), P(C.c_double), C.c_double,
+                                        P(_Params), P(C.c_int64), P(C.c_int32)]
+        L.mlo_implicit_leap.restype = C.c_int
         L.mlo_lane_tree_sum.argtypes = [P(C.c_double), C.c_int32]
         L.mlo_lane_tree_sum.restype = C.c_double
         L.mlo_implicit_solve.argtypes = [C.c_int32, C.c_int32, P(C.c_int32), P(C.c_int32),
@@ -227,6 +242,50 @@ def tau_select(crn, a, x, use=None, eps=0.03):
     return lib().mlo_tau_select(crn.n_species, crn.n_reactions, _p(crn.orders, C.c_int32),
                                 _p(crn.stoich, C.c_int32), _p(a, C.c_double),
                                 _p(x, C.c_int64), _p(use, C.c_uint8), eps)
+
+
+def critical_set(crn, a, x, n_c=10):
+    """Returns (crit mask as a bool array, ac, a0c)."""
+    a = np.ascontiguousarray(a, np.float64)
+    x = np.ascontiguousarray(x, np.int64)
+    crit = np.zeros(crn.n_reactions, np.uint8)
+    ac = np.zeros(crn.n_reactions)
+    a0c = lib().mlo_critical_set(crn.n_species, crn.n_reactions, _p(crn.orders, C.c_int32),
+                                 _p(crn.stoich, C.c_int32), _p(a, C.c_double), _p(x, C.c_int64),
+                                 int(n_c), _p(crit, C.c_uint8), _p(ac, C.c_double))
+    return crit.astype(bool), ac, a0c
+
+
+def pick(w, target):
+    w = np.ascontiguousarray(w, np.float64)
+    return int(lib().mlo_pick(w.size, _p(w, C.c_double), float(target)))
+
+
+def ssa_switch(tau1, tau2, a0, ssa_factor):
+    return bool(lib().mlo_ssa_switch(float(tau1), float(tau2), float(a0), float(ssa_factor)))
+
+
+def implicit_count(a_y, tau, P, a_x):
+    return int(lib().mlo_implicit_count(float(a_y), float(tau), float(P), float(a_x)))
+
+
+def implicit_leap(crn, theta, x, nc, P, a_x, tau, params: Params | None = None):
+    """Returns (rc, K, iterations); K of reactions with nc = 0 is left at 0."""
+    params = params or Params()
+    theta = np.ascontiguousarray(theta, np.float64)
+    x = np.ascontiguousarray(x, np.int64)
+    nc = np.ascontiguousarray(nc, np.uint8)
+    P = np.ascontiguousarray(P, np.float64)
+    a_x = np.ascontiguousarray(a_x, np.float64)
+    K = np.zeros(crn.n_reactions, np.int64)
+    its = C.c_int32(0)
+    pc = params.c()
+    rc = lib().mlo_implicit_leap(crn.n_species, crn.n_reactions, _p(crn.orders, C.c_int32),
+                                 _p(crn.stoich, C.c_int32), _p(theta, C.c_double),
+                                 _p(x, C.c_int64), _p(nc, C.c_uint8), _p(P, C.c_double),
+                                 _p(a_x, C.c_double), float(tau), C.byref(pc), _p(K, C.c_int64),
+                                 C.byref(its))
+    return rc, K, int(its.value)
 
 
 def implicit_solve(crn, theta, x, nc, P, a_x, tau, params: Params | None = None):
