@@ -1,22 +1,27 @@
 #!/usr/bin/env python
 """Benchmark: ensembles of adaptive tau-leaping trajectories on one GPU per rank.
 
-Workload (default): the stiff decaying-dimerising network (3 species, 4 reactions,
-S1 -> 0, 2 S1 -> S2, S2 -> 2 S1, S2 -> S3 with rates 1, 10, 1000, 0.1), x0 = (400, 798, 0),
-T = 0.2, eps = 0.03, n_c = 10, 100,000 trajectories per GPU (weak scaling: rank k simulates
-trajectory ids [k B, (k+1) B)).
+Workload (default): the batched particle-filter workload -- two-state gene expression,
+3 species, 6 reactions, per-trajectory rate constants theta_j ~ Gamma(2, 2/theta_true_j)
+and horizons T ~ U[50, 200], x0 = 0, eps = 0.03, n_c = 10, 1,000,000 trajectories per GPU
+(weak scaling: rank k simulates trajectory ids [k B, (k+1) B)).  --config selects another
+workload (0 immigration-death, 1 stiff dimerisation, 3 random 50 x 100 network).
 
 A step is one simulate call over the whole batch.  Two forms are timed:
-  batched  fast precision (FP32 propensities, step sizes, Poisson means and implicit
-           Newton solve; FP64 time and G totals), persistent refill kernel launched from
-           a CUDA graph, autotuned shape  -> the headline `value`;
-  plain    reference precision (FP64 everywhere), one launch, one thread per trajectory.
+  batched  fast precision (FP32 propensities, step sizes, Poisson means and G
+           increments; FP64 time, G totals and implicit Newton solve), persistent refill
+           kernel launched from a CUDA graph, autotuned shape  -> the headline `value`;
+  plain    reference precision (FP64 everywhere), one launch, one thread per trajectory
+           (`plain_fp64`, timed for at most --plain-budget-s seconds, at least 2 steps).
 Inputs are resident in HBM when timing starts; a 256 MB buffer is written between steps to
 flush L2.  `e2e` times the host-buffer entry point (pinned host memory, copies inside).
 `cpu_baseline` times the CPU oracle on one host core on a bounded sample and
-`cpu_baseline_all_cores` as one process per core; `roofline` reports the algorithmic and
-the issue-rate view, `pipe_peaks` the measured pipe throughputs, `bayes_step` the
-posterior draw and resampling, `accuracy` the paper's KL study (Section 3, Table 1).
+`cpu_baseline_all_cores` as one process per core; `parity` compares the last timed step
+with the oracle on the same ids; `roofline` reports the algorithmic and the issue-rate
+view; `other_workloads` repeats the fast form with FP64 and FP32 Newton solves and the
+plain form on the stiff dimerisation; `pipe_peaks` the measured pipe throughputs,
+`bayes_step` the posterior draw and resampling, `accuracy` the paper's KL study (Section 3,
+Table 1), `serving` the continuous-batching mix.
 `--impl reference` times only the oracle (the reference arm for this method).
 """
 import argparse
@@ -43,22 +48,31 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--n-traj", type=int, default=None)
     ap.add_argument("--horizon", type=float, default=None,
                     help="override the workload's horizon T (one value for every trajectory)")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0,
                     help="target CPU seconds for the oracle baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--jacobian", choices=["fd", "analytic"], default="analytic",
+    ap.add_argument("--jacobian", choices=["fd", "analytic"], default="fd",
                     help="Jacobian of the implicit solve, same for both forms")
+    ap.add_argument("--newton", choices=["fp64", "fp32"], default="fp64",
+                    help="arithmetic of the fast precision's implicit Newton solve")
+    ap.add_argument("--plain-budget-s", type=float, default=60.0,
+                    help="the plain FP64 form stops timing after this many seconds (>= 2 steps)")
+    ap.add_argument("--e2e-budget-s", type=float, default=20.0,
+                    help="the end-to-end leg stops timing after this many seconds (>= 2 steps)")
+    ap.add_argument("--extra-configs", default="1",
+                    help="comma-separated workloads measured beside the headline")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default launch shape (for very long workloads)")
     ap.add_argument("--shape", type=int, default=0,
                     help="force a launch shape (ML_SHAPE_*; skips the autotuner)")
     ap.add_argument("--block", type=int, default=0, help="force threads per CTA")
-    ap.add_argument("--serving-seconds", type=float, default=4.0,
+    ap.add_argument("--serving-seconds", type=float, default=60.0,
                     help="arrival window of the serving mix (0 = skip it)")
     ap.add_argument("--ncu", action="store_true",
                     help="skip the CPU leg, autotune, e2e and clocks (for profiler runs)")
@@ -132,13 +146,11 @@ POISSON_INV_OPS = 40  # exp, ~3 search steps of 3 ops, uniform
 POISSON_PTRS_OPS = 110
 NEWTON_ITERATIONS = 4.3  # mean iterations per implicit leap on dimerisation states (oracle)
 
-# Per-launch figures measured by ncu for the kernels the default workload runs, keyed by
-# (config, shape): DRAM bytes read + written, warp instructions issued, FP64-pipe busy
-# fraction (profiles/k_thread_fast_dimerisation_100k.md).  Absent: reported as null.
-PROFILED = {
-    (1, 5): {"dram_bytes": 305_408 + 158_976, "warp_inst": 375_367_574, "fp64_pipe_pct": 14.52},
-    (1, 4): {"dram_bytes": 160_512 + 5_120, "warp_inst": 350_663_978, "fp64_pipe_pct": 10.58},
-}
+# Per-launch figures measured by ncu for the headline kernel, keyed by (config, shape,
+# threads per CTA) of the launch the bench times: DRAM bytes read + written, warp
+# instructions issued and FP64-pipe busy fraction, with the capture they come from (a
+# profiles/ summary).  A launch shape without a capture of the current kernel reports null.
+PROFILED = {}
 
 
 def work_model(crn):
@@ -347,17 +359,30 @@ def run_serving(ml, seconds, rate_hz=200.0, seed=11, max_inflight=8, budget=8 <<
         h.free()
     srv.close()
     lat = np.array(lat)
+    span = reqs[-1]["arrival_s"] - reqs[0]["arrival_s"]
     return {"requests": len(reqs), "arrival_rate_hz": rate_hz, "window_s": seconds,
             "trajectories": int(total_traj),
-            "models": "immigration-death, dimerisation, gene expression, random 50x100 (horizons scaled, see workloads.SERVING_HORIZON_SCALE)",
+            "offered_traj_per_s": total_traj / max(span, 1e-9),
+            "models": "immigration-death, dimerisation, gene expression, random 50x100",
+            "horizon_scale": {W.config(m, n_traj=1).name: W.SERVING_HORIZON_SCALE[m] for m in models},
+            "theta_gamma_shape": {W.config(m, n_traj=1).name: W.SERVING_THETA_SHAPE[m] for m in models},
+            "why_scaled": "at 200 requests/s of 1e3-1e5 trajectories each model is offered "
+                          "about 1.07e6 trajectories/s; at its benchmark horizon gene "
+                          "expression would need 2.3 GPUs and the 50 x 100 network about "
+                          "5,000, so each model's horizon is scaled to a fraction of one GPU",
             "p50_latency_ms": 1e3 * float(np.percentile(lat, 50)),
             "p99_latency_ms": 1e3 * float(np.percentile(lat, 99)),
             "sustained_traj_per_s": total_traj / makespan,
+            "sustained_vs_one_request_per_launch": (total_traj / makespan) / seq["sustained_traj_per_s"],
+            "p99_latency_vs_one_request_per_launch": float(np.percentile(lat, 99)) * 1e3 / seq["p99_latency_ms"],
             "saturated_traj_per_s": total_traj / drain,
             "saturated_vs_one_request_per_launch": (total_traj / drain) / (total_traj / sum(service)),
             "peak_inflight": st["peak_inflight"], "max_inflight": max_inflight,
             "peak_device_bytes": st["peak_bytes"], "budget_bytes": budget,
-            "one_request_per_launch": seq}
+            "one_request_per_launch": seq,
+            "note": "sustained = all trajectories / (last completion - first arrival) at the "
+                    "offered load; one request per launch is timed request by request and "
+                    "queued by the same arrival times"}
 
 
 # ---------------------------------------------------------------------------------
@@ -474,6 +499,89 @@ def run_accuracy(ml, n=10_000, K=20, replicates=5, seed=500):
         "averaged over time points and species (Section 3, Table 1)")}
 
 
+SHAPE_NAMES = {1: "thread, round-based", 2: "warp", 3: "thread, round-based, occupancy build",
+               4: "thread, sequential per lane", 5: "thread, sequential per lane, occupancy build"}
+
+
+def precision_label(ml, p):
+    """What the fast kernels compute in which arithmetic, from the parameters used."""
+    jac = "forward-difference" if p.jacobian == ml.ML_JAC_FD else "exact"
+    if p.newton_precision == ml.ML_NEWTON_FP32:
+        newton = ("FP32 Newton solve for the increment z = y - x (exact Jacobian) in the "
+                  "thread kernel, FP32 factorization under an FP64 residual in the warp kernel")
+    else:
+        newton = f"FP64 Newton solve ({jac} Jacobian, pivoted elimination, rounding)"
+    return ("FP32 propensities, step sizes, Poisson means and G increments; FP64 time and G "
+            f"totals; {newton}; int64 counts")
+
+
+class Bench:
+    """Timing helpers shared by the headline workload and the extra workloads."""
+
+    def __init__(self, ml, dev, stream, args, world, barrier):
+        import torch
+        self.ml, self.dev, self.stream, self.args = ml, dev, stream, args
+        self.world, self.barrier = world, barrier
+        self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
+
+    def outputs(self, model, B):
+        import torch
+        d = self.dev
+        return {"X": torch.empty((B, model.N), dtype=torch.int64, device=d),
+                "r": torch.empty((B, model.M), dtype=torch.int64, device=d),
+                "G": torch.empty((B, model.M), dtype=torch.float64, device=d),
+                "status": torch.empty((B,), dtype=torch.int32, device=d),
+                "counters": torch.empty((B, 4), dtype=torch.int64, device=d)}
+
+    def timed(self, model, B, x0, T, theta, params, seed0, id_base, steps, warmup,
+                      budget_s=None, min_steps=2):
+        """`warmup` full untimed steps (or, with warmup = 0, one launch on a 4,096-trajectory
+        prefix), then timed steps: `steps` of them, or fewer once budget_s seconds of timed
+        work have passed (never fewer than min_steps).  L2 is flushed before every step;
+        each step is bracketed by CUDA events on the launching stream."""
+        import torch
+        ml, stream = self.ml, self.stream
+        out = self.outputs(model, B)
+        for s in range(warmup):
+            ml.ml_simulate(model, B, x0, T, theta, params=params, seed=seed0 + s,
+                           traj_id_base=id_base, out=out)
+        if warmup == 0:
+            n0 = min(B, 4096)
+            ml.ml_simulate(model, n0, x0 if x0.dim() == 1 else x0[:n0],
+                           T if T.numel() == 1 else T[:n0], None if theta is None else theta[:n0],
+                           params=params, seed=seed0, traj_id_base=id_base)
+        torch.cuda.synchronize()
+        acc = torch.zeros(4, dtype=torch.int64, device=self.dev)
+        evs, launches = [], 0
+        self.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = 0
+        while k < steps:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            self.flush.zero_()
+            e0.record(stream)
+            ml.ml_simulate(model, B, x0, T, theta, params=params, seed=seed0 + warmup + k,
+                           traj_id_base=id_base, out=out)
+            e1.record(stream)
+            evs.append((e0, e1))
+            launches += ml.ml_model_last_launch_count(model)
+            acc += out["counters"].sum(0)
+            k += 1
+            if budget_s is not None and k >= min_steps:
+                e1.synchronize()
+                if time.perf_counter() - t0 > budget_s:
+                    break
+        torch.cuda.synchronize()
+        self.barrier()
+        wall = time.perf_counter() - t0
+        ms = [a.elapsed_time(b) for a, b in evs]
+        bad = int((out["status"] & ~(ml.ML_ST_NEWTON_FAIL | ml.ML_ST_PTRS_CAP)).ne(0).sum().item())
+        return {"ms": ms, "mean_ms": statistics.mean(ms), "counts": acc.cpu().numpy(),
+                "wall_s": wall, "steps": k, "launches": launches, "last_out": out,
+                "last_seed": seed0 + warmup + k - 1, "bad_status": bad}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -507,106 +615,94 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return t.cpu().numpy()
 
-    w = W.config(args.config, n_traj=args.n_traj)
-    if args.horizon is not None:
-        import numpy as np
-        w.T = np.array([args.horizon])
-    B = w.n_traj
-    id_base = rank * B
-    model = ml.model_from_crn(w.crn)
-    x0 = torch.as_tensor(w.x0, device=dev)
-    T = torch.as_tensor(w.T, device=dev)
-    theta = None if w.theta is None else torch.as_tensor(w.theta, device=dev)
     stream = torch.cuda.current_stream()
-
+    bench = Bench(ml, dev, stream, args, world, barrier)
     jac = ml.ML_JAC_ANALYTIC if args.jacobian == "analytic" else ml.ML_JAC_FD
-    fast = ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32, form=ml.ML_FORM_PERSISTENT,
-                                use_graph=1, max_steps=MAX_STEPS, jacobian=jac)
-    if args.shape:
-        fast.shape, fast.block_size = args.shape, args.block
-    elif not args.ncu and not args.no_autotune:
-        best = ml.ml_autotune(model, B, x0, T, theta, params=fast, n_sample=min(B, 100_000))
-        fast.shape, fast.block_size, fast.ctas_per_sm = best.shape, best.block_size, best.ctas_per_sm
-    # the plain form: one launch, each thread runs its trajectory to the end, FP64
-    plain = ml.ml_default_params(precision=ml.ML_PREC_REF_FP64, form=ml.ML_FORM_PLAIN,
-                                 max_steps=MAX_STEPS, block_size=128, jacobian=jac,
-                                 shape=ml.ML_SHAPE_THREAD_SEQ if W.config(args.config, n_traj=1).crn.n_reactions <= 16
-                                 else ml.ML_SHAPE_WARP)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
+    newton = ml.ML_NEWTON_FP32 if args.newton == "fp32" else ml.ML_NEWTON_FP64
 
-    def timed(params, seed0):
-        out = {"X": torch.empty((B, model.N), dtype=torch.int64, device=dev),
-               "r": torch.empty((B, model.M), dtype=torch.int64, device=dev),
-               "G": torch.empty((B, model.M), dtype=torch.float64, device=dev),
-               "status": torch.empty((B,), dtype=torch.int32, device=dev),
-               "counters": torch.empty((B, 4), dtype=torch.int64, device=dev)}
-        for s in range(args.warmup):
-            ml.ml_simulate(model, B, x0, T, theta, params=params, seed=seed0 + s,
-                           traj_id_base=id_base, out=out)
-        torch.cuda.synchronize()
-        acc = torch.zeros(4, dtype=torch.int64, device=dev)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        launches = 0
-        barrier()
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_push("timed")
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()
-            evs[k][0].record(stream)
-            ml.ml_simulate(model, B, x0, T, theta, params=params, seed=seed0 + args.warmup + k,
-                           traj_id_base=id_base, out=out)
-            evs[k][1].record(stream)
-            launches += ml.ml_model_last_launch_count(model)
-            acc += out["counters"].sum(0)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-        barrier()
-        wall = time.perf_counter() - t0
-        ms = [a.elapsed_time(b) for a, b in evs]
-        bad = int((out["status"] & ~(ml.ML_ST_NEWTON_FAIL | ml.ML_ST_PTRS_CAP)).ne(0).sum().item())
-        return {"ms": ms, "mean_ms": statistics.mean(ms), "counts": acc.cpu().numpy(),
-                "wall_s": wall, "launches": launches, "last_out": out,
-                "last_seed": seed0 + args.warmup + args.steps - 1, "bad_status": bad}
+    def fast_params(newton_precision=newton):
+        return ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32, form=ml.ML_FORM_PERSISTENT,
+                                    use_graph=1, max_steps=MAX_STEPS, jacobian=jac,
+                                    newton_precision=newton_precision)
 
+    def plain_params(crn):
+        return ml.ml_default_params(precision=ml.ML_PREC_REF_FP64, form=ml.ML_FORM_PLAIN,
+                                    max_steps=MAX_STEPS, block_size=128, jacobian=jac,
+                                    shape=ml.ML_SHAPE_THREAD_SEQ if crn.n_reactions <= 16
+                                    else ml.ML_SHAPE_WARP)
+
+    def load(cfg, n_traj=None, horizon=None):
+        w = W.config(cfg, n_traj=n_traj)
+        if horizon is not None:
+            w.T = np.array([horizon])
+        model = ml.model_from_crn(w.crn)
+        x0 = torch.as_tensor(w.x0, device=dev)
+        T = torch.as_tensor(w.T, device=dev)
+        theta = None if w.theta is None else torch.as_tensor(w.theta, device=dev)
+        return w, model, x0, T, theta
+
+    def tune(model, B, x0, T, theta, p):
+        if args.shape:
+            p.shape, p.block_size, p.ctas_per_sm = args.shape, args.block, 0
+        elif not args.ncu and not args.no_autotune:
+            best = ml.ml_autotune(model, B, x0, T, theta, params=p, n_sample=min(B, 100_000))
+            p.shape, p.block_size, p.ctas_per_sm = best.shape, best.block_size, best.ctas_per_sm
+        return p
+
+    def shape_of(p):
+        return {"shape": SHAPE_NAMES.get(p.shape, "auto"), "shape_id": int(p.shape),
+                "block_size": int(p.block_size), "ctas_per_sm": int(p.ctas_per_sm)}
+
+    # ---------------- the headline workload
+    w, model, x0, T, theta = load(args.config, args.n_traj, args.horizon)
+    B = w.n_traj
+    # weak scaling: rank k simulates ids [k B, (k+1) B) of a world x B batch
+    id_base, _ = ml.shard_bounds(world * B, rank, world)
+    fast = tune(model, B, x0, T, theta, fast_params())
     clocks = ClockSampler(local)
     if not args.ncu:
         clocks.start()
-    res_fast = timed(fast, 1000)
+    res_fast = bench.timed(model, B, x0, T, theta, fast, 1000, id_base, args.steps,
+                                   args.warmup)
     clk = clocks.stop() if not args.ncu else None
-    res_plain = None if args.no_plain else timed(plain, 5000)
-
     ms_fast = max_over_ranks(res_fast["mean_ms"])
-    counts_fast = sum_over_ranks(res_fast["counts"].astype(np.float64)) / args.steps
+    counts_fast = sum_over_ranks(res_fast["counts"].astype(np.float64)) / res_fast["steps"]
     value = world * B / (ms_fast / 1e3)
     leap_steps = float(counts_fast[0] + counts_fast[1] + counts_fast[2])
     line = {"metric": METRIC, "value": value, "unit": "trajectories/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_fast,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": workload_name(w), "form": "persistent refill kernel, CUDA graph, autotuned",
-                       "precision": "FP32 propensities/tau/Poisson, FP64 t/G/Newton",
-                       "jacobian": args.jacobian,
-                       "shape": {"shape": {ml.ML_SHAPE_THREAD: "thread, round-based", ml.ML_SHAPE_WARP: "warp",
-                                           ml.ML_SHAPE_THREAD_OCC: "thread, round-based, occupancy build",
-                                           ml.ML_SHAPE_THREAD_SEQ: "thread, sequential per lane",
-                                           ml.ML_SHAPE_THREAD_SEQ_OCC: "thread, sequential per lane, occupancy build"}.get(fast.shape, "auto"),
-                                 "block_size": fast.block_size, "ctas_per_sm": fast.ctas_per_sm},
+            "config": {"workload": workload_name(w),
+                       "form": "persistent refill kernel, CUDA graph, autotuned",
+                       "precision": precision_label(ml, fast),
+                       "jacobian": args.jacobian, "shape": shape_of(fast),
                        "l2": "flushed between steps (256 MB write)"},
             "leap_steps_per_s": leap_steps / (ms_fast / 1e3),
-            "mode_mix_per_step": {"explicit_leaps": float(counts_fast[0]), "implicit_leaps": float(counts_fast[1]),
-                                  "ssa_firings": float(counts_fast[2]), "rejected_leaps": float(counts_fast[3])},
+            "accepted_leaps_per_s": float(counts_fast[0] + counts_fast[1]) / (ms_fast / 1e3),
+            "ssa_steps_per_s": float(counts_fast[2]) / (ms_fast / 1e3),
+            "mode_mix_per_step": {"explicit_leaps": float(counts_fast[0]),
+                                  "implicit_leaps": float(counts_fast[1]),
+                                  "ssa_firings": float(counts_fast[2]),
+                                  "rejected_leaps": float(counts_fast[3])},
             "gpu_launches": int(res_fast["launches"])}
-    if res_plain is not None:
-        ms_plain = max_over_ranks(res_plain["mean_ms"])
-        counts_plain = sum_over_ranks(res_plain["counts"].astype(np.float64)) / args.steps
-        line["plain_fp64"] = {"value": world * B / (ms_plain / 1e3), "unit": "trajectories/s",
-                              "ms_per_step": ms_plain,
-                              "leap_steps_per_s": float(counts_plain[:3].sum()) / (ms_plain / 1e3),
-                              "form": "one launch, one thread per trajectory run to its end, FP64 reference precision"}
+
+    def plain_leg(model, B, x0, T, theta, crn, seed0, budget_s):
+        res = bench.timed(model, B, x0, T, theta, plain_params(crn), seed0, id_base,
+                                  args.steps, 0, budget_s=budget_s)
+        msp = max_over_ranks(res["mean_ms"])
+        cnt = sum_over_ranks(res["counts"].astype(np.float64)) / res["steps"]
+        return {"value": world * B / (msp / 1e3), "unit": "trajectories/s", "ms_per_step": msp,
+                "steps": res["steps"],
+                "warmup": "one untimed launch on a 4,096-trajectory prefix",
+                "leap_steps_per_s": float(cnt[:3].sum()) / (msp / 1e3),
+                "gpu_launches": int(res["launches"]),
+                "form": "one launch, one thread (warp for the 50 x 100 network) per trajectory "
+                        "run to its end, FP64 reference precision"}
+
+    if not args.no_plain:
+        line["plain_fp64"] = plain_leg(model, B, x0, T, theta, w.crn, 5000, args.plain_budget_s)
         line["batched_vs_plain"] = line["value"] / line["plain_fp64"]["value"]
-        line["gpu_launches_plain"] = int(res_plain["launches"])
 
     # roofline of the headline kernel: algorithmic operations against the issue rate
     ops_model = work_model(w.crn)
@@ -616,16 +712,16 @@ def run_ours(args):
     peak_clock = 2070.0
     peak = sms * 128 * peak_clock * 1e6 / 1e12   # Tops/s: SMs x 4 schedulers x 32 lanes x clock
     achieved = ops_per_launch / (ms_fast / 1e3) / 1e12
-    prof = PROFILED.get((args.config, fast.shape), {}) if args.n_traj is None else {}
-    traffic = prof.get("dram_bytes")
+    prof = PROFILED.get((args.config, int(fast.shape), int(fast.block_size)), {}) \
+        if (args.n_traj is None and args.horizon is None) else {}
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                        "frac": achieved / peak, "traffic": traffic,
+                        "frac": achieved / peak, "traffic": prof.get("dram_bytes"),
+                        "traffic_source": prof.get("source"),
                         "algorithmic_bytes_per_launch": int(B * (8 * model.N + 16 * model.M + 36)
-                                                            + (0 if theta is None else B * 8 * model.M)),
-                        "peak_basis": f"{sms} SMs x 128 lanes x {peak_clock:.0f} MHz (issue rate, one op per lane per clock)",
+                                                            + (0 if theta is None else B * 8 * model.M)
+                                                            + (0 if w.T.size == 1 else B * 8)),
+                        "peak_basis": f"{sms} SMs x 128 lanes x {peak_clock:.0f} MHz (one operation per lane per clock; measured FP32 FMA rate in pipe_peaks)",
                         "work_model_ops_per_event": ops_model}
-    # issue-rate view: warp instructions the kernel issues per launch (ncu) against
-    # SMs x 4 schedulers x one warp instruction per clock
     inst = prof.get("warp_inst")
     issue_peak = sms * 4 * peak_clock * 1e6
     line["roofline"]["issue"] = {
@@ -647,20 +743,24 @@ def run_ours(args):
                 "G": torch.empty((B, model.M), dtype=torch.float64).pin_memory(),
                 "status": torch.empty((B,), dtype=torch.int32).pin_memory(),
                 "counters": torch.empty((B, 4), dtype=torch.int64).pin_memory()}
-        for s in range(args.warmup):
-            ml.ml_simulate_host(model, B, hx0, hT, hth, params=fast, seed=s, traj_id_base=id_base,
-                                out=hout, stream=stream)
+        ml.ml_simulate_host(model, B, hx0, hT, hth, params=fast, seed=99, traj_id_base=id_base,
+                            out=hout, stream=stream)
         barrier()
         t0 = time.perf_counter()
-        for k in range(args.steps):
+        k = 0
+        while k < args.steps:
             ml.ml_simulate_host(model, B, hx0, hT, hth, params=fast, seed=100 + k,
                                 traj_id_base=id_base, out=hout, stream=stream)
+            k += 1
+            if k >= 2 and time.perf_counter() - t0 > args.e2e_budget_s:
+                break
         barrier()
-        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / k)
         h2d = hx0.numel() * 8 + hT.numel() * 8 + (0 if hth is None else hth.numel() * 8)
         d2h = sum(v.numel() * v.element_size() for v in hout.values())
         line["e2e"] = {"value": world * B / e2e_s, "unit": "trajectories/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "steps": k, "warmup": 1,
                        "path": "ml_simulate_host: pinned host inputs -> device -> simulate -> host"}
 
     # CPU oracle baseline and oracle-matched statistics (rank 0, N = 1 only for the baseline)
@@ -682,7 +782,39 @@ def run_ours(args):
         g = {k: v[:n].cpu().numpy() for k, v in res_fast["last_out"].items()}
         rows = stats_util.compare(g, oout, g_res=stats_util.G_RESOLUTION_FAST)
         line["parity"] = {"fast_vs_oracle": stats_util.summary(rows), "n_compared": n,
+                          "ids": f"first {n} trajectory ids of the last timed step, same seed",
                           "bad_status": res_fast["bad_status"]}
+        line["parity"]["holm_pass_0.01"] = line["parity"]["fast_vs_oracle"]["holm_pass_0.01"]
+
+    # the other workloads, each as a whole: fast (FP64 and FP32 Newton) and plain FP64
+    extras = {}
+    for cfg in [int(c) for c in args.extra_configs.split(",") if c.strip()]:
+        if cfg == args.config or args.ncu:
+            continue
+        we, me, x0e, Te, the = load(cfg)
+        Be = we.n_traj
+        entry = {"workload": workload_name(we)}
+        for key, nw in (("fast_fp64_newton", ml.ML_NEWTON_FP64), ("fast_fp32_newton", ml.ML_NEWTON_FP32)):
+            pe = tune(me, Be, x0e, Te, the, fast_params(nw))
+            r = bench.timed(me, Be, x0e, Te, the, pe, 2000, id_base, args.steps,
+                                    args.warmup, budget_s=30.0)
+            mse = max_over_ranks(r["mean_ms"])
+            ce = sum_over_ranks(r["counts"].astype(np.float64)) / r["steps"]
+            opse = ops_from_counts(work_model(we.crn), ce / world)
+            entry[key] = {"value": world * Be / (mse / 1e3), "unit": "trajectories/s",
+                          "ms_per_step": mse, "steps": r["steps"], "warmup": args.warmup,
+                          "leap_steps_per_s": float(ce[:3].sum()) / (mse / 1e3),
+                          "mode_mix_per_step": [float(v) for v in ce],
+                          "precision": precision_label(ml, pe), "shape": shape_of(pe),
+                          "roofline_frac": opse / (mse / 1e3) / 1e12 / peak,
+                          "bad_status": r["bad_status"]}
+        if not args.no_plain:
+            entry["plain_fp64"] = plain_leg(me, Be, x0e, Te, the, we.crn, 6000, 30.0)
+            entry["batched_vs_plain"] = entry["fast_fp64_newton"]["value"] / entry["plain_fp64"]["value"]
+        extras[we.name] = entry
+    if extras:
+        line["other_workloads"] = extras
+
     if rank == 0 and world == 1 and not args.ncu:
         pk = ml.ml_measure_pipe_peaks()
         line["pipe_peaks"] = {"fp64_fma_tflops": pk["fp64_fma_flops"] / 1e12,
@@ -691,7 +823,8 @@ def run_ours(args):
                               "note": "project microbenchmarks (8 independent chains per thread, "
                                       "8 CTAs of 256 threads per SM, ~20 ms each)"}
         line["bayes_step"] = run_bayes(ml, res_fast["last_out"])
-        line["accuracy"] = run_accuracy(ml)
+        if not args.no_accuracy:
+            line["accuracy"] = run_accuracy(ml)
     if rank == 0 and world == 1 and args.serving_seconds > 0 and not args.ncu:
         line["serving"] = run_serving(ml, args.serving_seconds)
     if rank == 0:

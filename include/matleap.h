@@ -58,6 +58,11 @@ extern "C" {
 #define ML_ST_PTRS_CAP 8u      /* a Poisson draw hit its trial cap                       */
 #define ML_ST_BAD_INPUT 16u    /* negative x0 or theta, or a NaN: trajectory not run     */
 #define ML_ST_STAGE_TIMEOUT 32u /* model staging wait ran out; plain loads were used     */
+#define ML_ST_OVERFLOW 64u     /* counts would leave the exact int64 range: the trajectory
+                                  stopped early (state and statistics as at the stop)
+                                  because, at the start of a step, a count or firing total
+                                  exceeded 2^62, or a leap's Poisson mean or an implicit
+                                  firing count exceeded 2^48                             */
 
 /* ---- modes (Section 3: matLeap can also run fully explicit or as SSA) -------------- */
 #define ML_MODE_ADAPTIVE 0      /* explicit / implicit / SSA switching                  */
@@ -67,8 +72,9 @@ extern "C" {
 /* ---- arithmetic ------------------------------------------------------------------- */
 #define ML_PREC_REF_FP64 0  /* FP64 everywhere, fixed operation order, no FMA: per
                                trajectory bit-identical to the CPU reference            */
-#define ML_PREC_FAST_FP32 1 /* FP32 propensities, step sizes and Poisson means; FP64
-                               time, G accumulation and implicit Newton solve          */
+#define ML_PREC_FAST_FP32 1 /* FP32 propensities, step sizes, Poisson means and G
+                               increments; FP64 time and G totals; the implicit Newton
+                               solve in FP64 (default) or FP32 (newton_precision)      */
 
 /* ---- launch forms ----------------------------------------------------------------- */
 #define ML_FORM_PLAIN 0      /* one launch, one thread (or warp) per trajectory         */
@@ -90,11 +96,19 @@ extern "C" {
                                      in the occupancy build                           */
 
 /* ---- Jacobian of the implicit solve (Section 1: estimated numerically, or the
- *      symbolic Jacobian of Section 3).  Reference precision and the warp kernel follow
- *      the choice; the fast-precision thread kernel always uses the exact derivative
- *      (there the Jacobian only sets the convergence rate, not the solution). -------- */
+ *      symbolic Jacobian of Section 3).  Every FP64 solve follows the choice; the FP32
+ *      increment solve of the fast thread kernel (ML_NEWTON_FP32) always uses the exact
+ *      derivative (there the Jacobian only sets the convergence rate). --------------- */
 #define ML_JAC_FD 0       /* forward differences                                          */
 #define ML_JAC_ANALYTIC 1 /* exact derivative of the mass-action polynomials              */
+
+/* ---- arithmetic of the implicit Newton solve in fast precision (reference precision
+ *      always solves in FP64) ------------------------------------------------------ */
+#define ML_NEWTON_FP64 0 /* FP64 propensities at x and y, residual, Jacobian, elimination
+                            and rounding (the default)                                 */
+#define ML_NEWTON_FP32 1 /* FP32: the thread kernel solves for the increment z = y - x
+                            (no cancellation of propensities of size a tau), the warp
+                            kernel factorizes the Jacobian in FP32 under an FP64 residual */
 
 typedef struct ml_model ml_model;
 
@@ -103,7 +117,7 @@ typedef struct ml_model ml_model;
  * pe_delta 0.05, stiff_ratio 100, newton_tol 1e-10, newton_maxit 20, fd_h 1e-7,
  * max_steps 1e8, max_reject 64, mode ADAPTIVE, precision REF_FP64, form PLAIN,
  * shape AUTO, block_size 0 (tuned or default), ctas_per_sm 0, use_graph 0,
- * jacobian FD. */
+ * jacobian FD, newton_precision FP64, stage_poll_limit 4194304, eval_quorum 4. */
 typedef struct {
   double eps;             /* Cao 2006 bound on the relative change of each reactant    */
   int32_t n_c;            /* critical threshold (Section 2)                            */
@@ -125,6 +139,16 @@ typedef struct {
   int32_t ctas_per_sm;    /* persistent form: resident CTAs per SM; 0 = tuned/default  */
   int32_t use_graph;      /* persistent form: launch through a cached CUDA graph       */
   int32_t jacobian;       /* ML_JAC_*: Jacobian of the propensities in implicit leaps  */
+  int32_t newton_precision; /* ML_NEWTON_*: fast precision's implicit solve            */
+  int32_t stage_poll_limit; /* polls of each thread's wait for the bulk copy of the
+                               model tables before the CTA falls back to plain loads
+                               and sets ML_ST_STAGE_TIMEOUT (>= 0; 0 forces the
+                               fallback, which tests use to exercise it)               */
+  int32_t eval_quorum;    /* round-based thread shapes: a round runs the leap-evaluation
+                               phase when at least this many of a warp's lanes need it (or
+                               none is inside an SSA burst), else a slice of the bursts;
+                               0 runs both phases every round.  Results do not depend on
+                               it.  0..32, default 4                                    */
 } ml_sim_params;
 
 /* Fills *p with the defaults above.  Returns ML_ERR_ARG if p is NULL. */
@@ -183,11 +207,12 @@ int ml_simulate_host(ml_model* model, int64_t n_traj, const double* theta,
                      uint32_t* status_out, int64_t* counters_out, void* cuda_stream);
 
 /* Project autotuner: times candidate kernel shapes (trajectory per thread or per warp,
- * threads per CTA, resident CTAs per SM) on the first min(n_traj, n_sample)
- * trajectories of the given inputs, with p's mode/precision/form (one warm-up run, then
- * the faster of two timed runs per candidate), and stores the
- * fastest in the model (used when a later call passes block_size = 0) and in *best.
- * Synchronizes cuda_stream.  Uses internal scratch outputs. */
+ * threads per CTA, resident CTAs per SM up to what fits at once) on the first
+ * min(n_traj, n_sample) trajectories of the given inputs, with p's mode/precision/form
+ * (one warm-up run, then the median of five timed runs per candidate; candidates in a
+ * fixed order, a later one replacing the best so far only when more than 3 % faster),
+ * and stores the choice in the model (used when a later call passes block_size = 0) and
+ * in *best.  Synchronizes cuda_stream.  Uses internal scratch outputs. */
 int ml_autotune(ml_model* model, int64_t n_traj, const double* theta, const int64_t* x0,
                 int32_t x0_per_traj, const double* T, int32_t T_per_traj,
                 const ml_sim_params* p, uint64_t seed, int64_t n_sample,
@@ -203,16 +228,19 @@ int ml_autotune(ml_model* model, int64_t n_traj, const double* theta, const int6
  *   (p->form and p->use_graph are ignored).
  *   Its only scratch (the work-queue counter and a copy of the model tables) is a fixed
  *   4 KiB device array inside the library, reserved on every GPU that loads it until the
- *   process exits; at most 3840 bytes of model tables fit, i.e. at most 8 species and 16
- *   reactions.  Larger models are rejected with ML_ERR_ARG and a message naming the size.
- *   The first call on a device looks up the array's device address (with that device
- *   current), so make that first call before any stream capture.
+ *   process exits.  Each call launches two kernels on cuda_stream: one that zeroes the
+ *   counter and writes the model tables (passed by value as its parameter, so no host
+ *   memory is read by a copy) and the simulation.  Models with more than 8 species or 16
+ *   reactions (which need one warp per trajectory) are rejected with ML_ERR_ARG and a
+ *   message naming the size; p->shape = ML_SHAPE_WARP gives ML_ERR_UNSUPPORTED.
+ *   Every call looks up the array's device address for the current device; the first
+ *   call on a device also loads the library's module there, so make that first call
+ *   before any stream capture.
  *   Every call reuses the same array and overwrites what the previous call left there:
  *   calls whose kernels overlap on the GPU (other streams, other threads) race and must
  *   be serialized by the caller.
  *   Makes no cudaMalloc, cudaFree or other allocating call.
- * Errors: as ml_simulate, plus ML_ERR_UNSUPPORTED for models that need one warp per
- * trajectory. */
+ * Errors: as ml_simulate. */
 int ml_simulate_noalloc(const ml_model* model, int64_t n_traj, const double* theta,
                         const int64_t* x0, int32_t x0_per_traj, const double* T,
                         int32_t T_per_traj, const ml_sim_params* p, uint64_t seed,

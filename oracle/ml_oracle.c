@@ -679,7 +679,17 @@ int mlo_ssa_switch(double tau1, double tau2, double a0, double ssa_factor) {
 int64_t mlo_implicit_count(double a_y, double tau, double P, double a_x) {
   double v = (a_y * tau + P) - a_x * tau;
   double rv = round(v);
+  if (!(rv < 0x1p62)) return MLO_COUNT_LIMIT; /* beyond any leap limit (also NaN) */
   return rv > 0.0 ? (int64_t)rv : 0;
+}
+
+/* The count limits above: 1 when a count or a firing total exceeds MLO_COUNT_LIMIT. */
+static int counts_beyond_limit(const int64_t* x, int32_t N, const int64_t* r, int32_t M) {
+  for (int32_t s = 0; s < N; ++s)
+    if (x[s] > MLO_COUNT_LIMIT) return 1;
+  for (int32_t j = 0; j < M; ++j)
+    if (r[j] > MLO_COUNT_LIMIT) return 1;
+  return 0;
 }
 
 /* One implicit leap: solve for y (implicit_solve_md), then K[j] = mlo_implicit_count for
@@ -849,6 +859,10 @@ static void simulate_one(traj_t* tr) {
       tr->status |= MLO_ST_STEP_LIMIT;
       break;
     }
+    if (counts_beyond_limit(tr->x, N, tr->r, M)) {
+      tr->status |= MLO_ST_OVERFLOW;
+      break;
+    }
     /* 1. propensities */
     eval_props(tr);
     double a0 = mlo_lane_tree_sum(tr->a, M);
@@ -893,6 +907,7 @@ static void simulate_one(traj_t* tr) {
       }
     }
     /* 5.-7. attempt loop: draw tau2, SSA switch, leap, negativity check */
+    int overflow = 0;
     for (;;) {
       if (reject_run >= p->max_reject) {
         tr->status |= MLO_ST_REJECT_LIMIT;
@@ -923,6 +938,9 @@ static void simulate_one(traj_t* tr) {
         at_horizon = 1;
       }
       int crit_fire = (tau2 <= tau1) && (tau2 <= rem);
+      for (int32_t j = 0; j < M; ++j)
+        if (nc[j] && tr->a[j] * tau > MLO_LEAP_LIMIT) overflow = 1;
+      if (overflow) break;
       for (int32_t j = 0; j < M; ++j) K[j] = 0;
       if (crit_fire) {
         uint32_t w[4];
@@ -943,6 +961,9 @@ static void simulate_one(traj_t* tr) {
           step++;
           continue;
         }
+        for (int32_t j = 0; j < M; ++j)
+          if (nc[j] && (double)K[j] > MLO_LEAP_LIMIT) overflow = 1;
+        if (overflow) break;
       } else {
         for (int32_t j = 0; j < M; ++j)
           if (nc[j])
@@ -975,6 +996,10 @@ static void simulate_one(traj_t* tr) {
       tr->cnt[implicit_step ? 1 : 0] += 1;
       step++;
       reject_run = 0;
+      break;
+    }
+    if (overflow) {
+      tr->status |= MLO_ST_OVERFLOW;
       break;
     }
   }

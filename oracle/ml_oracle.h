@@ -34,6 +34,16 @@ extern "C" {
 #define MLO_ST_NEWTON_FAIL 2u  /* an implicit solve failed; explicit leap used instead */
 #define MLO_ST_REJECT_LIMIT 4u /* max_reject consecutive negativity rejections -> SSA  */
 #define MLO_ST_PTRS_CAP 8u     /* a Poisson draw hit the trial cap                     */
+#define MLO_ST_OVERFLOW 64u    /* counts left the exact int64 range: stopped early;
+                                  see mlo_count_limit / mlo_leap_limit                */
+
+/* Count limits: a trajectory stops (status MLO_ST_OVERFLOW, state and statistics as at
+ * the stop) when, at the start of an outer step, a count x_s or firing total r_j exceeds
+ * MLO_COUNT_LIMIT, or when a leap would draw a Poisson mean a_j tau, or an implicit leap
+ * would fire a reaction, more than MLO_LEAP_LIMIT times.  With at most 128 reactions and
+ * |nu| <= 127 every int64 sum then stays below 2^63. */
+#define MLO_COUNT_LIMIT 4611686018427387904LL /* 2^62 */
+#define MLO_LEAP_LIMIT 281474976710656.0      /* 2^48 */
 
 typedef struct {
   double eps;             /* Cao 2006 relative-change bound epsilon                  */
@@ -124,7 +134,8 @@ double mlo_critical_set(int32_t N, int32_t M, const int32_t* orders, const int32
 int32_t mlo_pick(int32_t M, const double* w, double target);
 /* The SSA switch: 1 iff min(tau1, tau2) < ssa_factor / a0. */
 int mlo_ssa_switch(double tau1, double tau2, double a0, double ssa_factor);
-/* Implicit firing count max(0, round((a_y tau + P) - a_x tau)), half away from zero. */
+/* Implicit firing count max(0, round((a_y tau + P) - a_x tau)), half away from zero,
+ * saturated at 2^62 (which exceeds MLO_LEAP_LIMIT, so the caller stops the trajectory). */
 int64_t mlo_implicit_count(double a_y, double tau, double P, double a_x);
 /* Implicit solve followed by mlo_implicit_count for every j with nc[j] (K_out of the
  * others untouched).  Returns the solve's code (0 converged, 1 not, 2 singular). */

@@ -147,12 +147,14 @@ __device__ __forceinline__ double log_factorial_ref(long long k) {
 
 // ---------------------------------------------------------------------------------
 // Model staging: one bulk asynchronous copy (TMA engine, cp.async.bulk) of the model
-// tables from global to shared memory, completed on an mbarrier.  The wait is bounded;
-// if it runs out the CTA copies the tables with plain loads and reports it.
+// tables from global to shared memory, completed on an mbarrier.  The wait is bounded
+// (poll_limit polls per thread); if it runs out the CTA waits again, bounded, for its copy
+// in flight, then copies the tables with plain loads and reports it.
 // bytes must be a multiple of 16 and both addresses 16-byte aligned.
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ bool stage_model_bulk(void* smem_dst, const void* gmem_src,
-                                                 uint32_t bytes, uint64_t* mbar) {
+                                                 uint32_t bytes, uint64_t* mbar,
+                                                 int poll_limit) {
   const uint32_t bar = (uint32_t)__cvta_generic_to_shared(mbar);
   const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem_dst);
   if (threadIdx.x == 0) {
@@ -171,9 +173,9 @@ __device__ __forceinline__ bool stage_model_bulk(void* smem_dst, const void* gme
         "l"(gmem_src), "r"(bytes), "r"(bar)
         : "memory");
   }
-  // every thread waits on phase 0, at most ~2^22 polls
+  // every thread waits on phase 0, at most poll_limit polls
   uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it) {
+  for (int it = 0; it < poll_limit && !done; ++it) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"

@@ -37,9 +37,11 @@ KernelEntry warp_entry_ref() {
 KernelEntry warp_grid_entry_ref() {
   return KernelEntry{&launch_grid, reinterpret_cast<const void*>(&k_warp<WPrec, true>)};
 }
-size_t warp_smem_bytes(int warps, int N, int M, int precision) {
-  const int rbytes = precision == ML_PREC_FAST_FP32 ? 4 : 8;
-  return (sizeof(WarpModel) + 15) / 16 * 16 + (size_t)warps * warp_slab_bytes(N, M, rbytes);
+size_t warp_smem_bytes(int warps, int N, int M, int precision, bool newton_fp32) {
+  const bool fast = precision == ML_PREC_FAST_FP32;
+  const int rbytes = fast ? 4 : 8;
+  const int lbytes = fast && newton_fp32 ? 4 : 8;
+  return (sizeof(WarpModel) + 15) / 16 * 16 + (size_t)warps * warp_slab_bytes(N, M, rbytes, lbytes);
 }
 #endif
 }  // namespace mlk

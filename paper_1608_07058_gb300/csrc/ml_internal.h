@@ -15,6 +15,13 @@ constexpr int kThreadVariants = 4;
 constexpr int kThreadN[kThreadVariants] = {1, 3, 3, 8};
 constexpr int kThreadM[kThreadVariants] = {2, 4, 6, 16};
 
+// Count limits (status ML_ST_OVERFLOW): a count or firing total above kCountLimit at the
+// start of a step, or a leap's Poisson mean or implicit firing count above kLeapLimit,
+// stops the trajectory; with M <= 128 and |nu| <= 127 every int64 sum stays below 2^63.
+constexpr long long kCountLimit = 1LL << 62;
+constexpr long long kLeapLimitInt = 1LL << 48;
+constexpr double kLeapLimit = 281474976710656.0;  // 2^48
+
 // Warp-per-trajectory capacities.
 constexpr int kWarpMaxN = 64;
 constexpr int kWarpMaxM = 128;
@@ -52,6 +59,11 @@ __host__ __device__ constexpr size_t thread_model_bytes() {
 // Model tables for the warp-per-trajectory kernels (compact sparse lists).
 struct alignas(16) WarpModel {
   double rates[kWarpMaxM];
+  // species bit masks (N <= 64): the reactants of reaction j, and the species reaction j
+  // changes.  After a firing of k, exactly the reactions j with rmask[j] & cmask[k] != 0
+  // have new propensities.
+  uint64_t rmask[kWarpMaxM];
+  uint64_t cmask[kWarpMaxM];
   int32_t N, M, n_pairs, nnz;
   // reactants of reaction j: up to 3 (species, multiplicity), increasing species
   int8_t rsp[kWarpMaxM][3];
@@ -102,6 +114,9 @@ struct SimArgs {
   int32_t max_reject;
   int32_t mode;
   int32_t jacobian;  // ML_JAC_*
+  int32_t newton_fp32;  // fast precision: FP32 implicit solve (ML_NEWTON_FP32)
+  int32_t stage_polls;  // bounded wait for the model-table bulk copy
+  int32_t eval_quorum;  // round-based thread driver: lanes needing an evaluation per round
   // persistent form: next unclaimed trajectory (zeroed before each launch)
   unsigned long long* queue;
   // time-grid output: K_obs observation times (nondecreasing, >= 0, finite; checked on the
@@ -161,8 +176,9 @@ KernelEntry warp_entry_ref();
 KernelEntry warp_entry_fast();
 KernelEntry warp_grid_entry_ref();
 KernelEntry warp_grid_entry_fast();
-// Dynamic shared memory of the warp kernel for a CTA of `warps` warps.
-size_t warp_smem_bytes(int warps, int N, int M, int precision);
+// Dynamic shared memory of the warp kernel for a CTA of `warps` warps (newton_fp32: fast
+// precision with an FP32 Newton system).
+size_t warp_smem_bytes(int warps, int N, int M, int precision, bool newton_fp32);
 
 // Launch description for the allocation-free entry point: everything is validated and
 // chosen by the host API without touching device memory; the caller copies host_tables

@@ -8,7 +8,7 @@
 // work-queue counter and a copy of the model tables -- in a fixed device array instead of
 // memory allocated on first use.  The caller still passes all inputs and outputs.
 #include <cstdint>
-#include <mutex>
+#include <cstring>
 
 #include <cuda_runtime.h>
 
@@ -21,29 +21,34 @@ namespace {
 // loads the library holds these 4 KiB until the process exits.
 constexpr size_t kScratchBytes = 4096;
 constexpr size_t kTablesOffset = 256;
-constexpr int kMaxDevices = 64;
+// The largest one-trajectory-per-thread table set (8 species x 16 reactions) is 432 bytes.
+constexpr size_t kTableParamBytes = 512;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex g_setup_mu;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
+// The model tables travel by value as a kernel parameter: the upload reads no pageable
+// host memory, needs no copy engine and allocates nothing, and like the simulation launch
+// after it, it is one kernel launch on the caller's stream.
+struct TableParam {
+  alignas(16) unsigned char b[kTableParamBytes];
+};
 
-// Device address of the scratch array on the current device, looked up once per device
-// with that device current (the array's name in host code is only a stand-in).
+// One CTA: zero the work-queue counter and write the tables behind it.
+__global__ void k_noalloc_setup(unsigned char* scratch, const TableParam t, uint32_t bytes) {
+  if (threadIdx.x == 0) *reinterpret_cast<unsigned long long*>(scratch) = 0ULL;
+  for (uint32_t k = threadIdx.x; k < bytes; k += blockDim.x) scratch[kTablesOffset + k] = t.b[k];
+}
+
+// Device address of the scratch array for the current device's context (the array's name
+// in host code is only a stand-in).  Looked up on every call: it is cheap, allocates
+// nothing, and stays right if the context is re-created.  The first lookup on a device
+// loads this module there.
 int scratch_address(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return mlk::set_error(ML_ERR_CUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return mlk::set_error(ML_ERR_UNSUPPORTED, "device index too large");
-  std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return mlk::set_error(ML_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
-    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_scratch_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return mlk::set_error(ML_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
+  *out = static_cast<unsigned char*>(p);
   return ML_OK;
 }
 
@@ -58,17 +63,19 @@ extern "C" int ml_simulate_noalloc(const ml_model* model, int64_t n_traj, const 
   mlk::NoAllocLaunch L;
   int rc = mlk::noalloc_prepare(model, n_traj, theta, x0, x0_per_traj, T, T_per_traj, p, seed,
                                 traj_id_base, X_out, r_out, G_out, status_out, counters_out,
-                                kScratchBytes - kTablesOffset, &L);
+                                kTableParamBytes, &L);
   if (rc != ML_OK) return rc;
   if (n_traj == 0) return ML_OK;
   unsigned char* scratch = nullptr;
   rc = scratch_address(&scratch);
   if (rc != ML_OK) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  // The array keeps the previous call's contents: reload the tables and zero the counter.
-  cudaError_t e = cudaMemcpyAsync(scratch + kTablesOffset, L.host_tables, L.table_bytes,
-                                  cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), s);
+  // The array keeps the previous call's contents: rewrite the tables and zero the counter.
+  TableParam tp;
+  std::memset(&tp, 0, sizeof tp);
+  std::memcpy(tp.b, L.host_tables, L.table_bytes);
+  k_noalloc_setup<<<1, 128, 0, s>>>(scratch, tp, (uint32_t)L.table_bytes);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return mlk::set_error(ML_ERR_CUDA, cudaGetErrorString(e));
   L.args.queue = reinterpret_cast<unsigned long long*>(scratch);
   e = L.entry.launch(scratch + kTablesOffset, L.args, L.grid, L.block, 0, s);

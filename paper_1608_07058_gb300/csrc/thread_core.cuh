@@ -1,9 +1,10 @@
 // One trajectory per thread: the adaptive explicit-implicit tau-leaping loop for small
 // networks (N <= 8 species, M <= 16 reactions), templated on the table capacities
 // (NM, MM) and on the arithmetic (P = PrecRef: FP64, fixed operation order, bitwise
-// reproducible; P = PrecFast: FP32 propensities/step sizes/Poisson means, FP64 time, G
-// and Newton).  All per-trajectory arrays are indexed with compile-time indices only so
-// that they live in registers.
+// reproducible; P = PrecFast: FP32 propensities, step sizes, Poisson means and G
+// increments, FP64 time and G totals, and an FP64 implicit Newton solve -- or, on
+// request, an FP32 solve for the increment).  All per-trajectory arrays are indexed with
+// compile-time indices only so that they live in registers.
 //
 // Steps (paper Section 2, with the published methods it names):
 //   propensities a_j = theta_j g_j(x), a0                       (Section 1)
@@ -37,6 +38,19 @@ __device__ __forceinline__ R lane_tree_sum(const R (&v)[MM]) {
     for (int l = 0; l < d; ++l) lane[l] = lane[l] + lane[l + d];
   }
   return lane[0];
+}
+
+// Sum over reactions: the canonical lane tree in reference precision (bitwise parity with
+// the CPU reference); fast precision may add in any order and adds sequentially (the tree
+// over 32 lanes costs 31 additions, most of them of zeros that IEEE arithmetic cannot
+// drop).
+template <int MM, class R, bool kRef>
+__device__ __forceinline__ R reaction_sum(const R (&v)[MM]) {
+  if (kRef) return lane_tree_sum<MM, R>(v);
+  R s = v[0];
+#pragma unroll
+  for (int j = 1; j < MM; ++j) s = s + v[j];
+  return s;
 }
 
 // C(v, m) for m = 1, 2, 3 on a real argument, in this operation order.
@@ -608,8 +622,13 @@ struct ThreadTraj {
 #pragma unroll
         for (int j = 0; j < MM; ++j) {
           if ((nc >> j) & 1u) {
-            const long long kj = K[j] + llroundf(tau * (th[j] * g_diff(md, j, xf, z)));
-            K[j] = kj > 0 ? kj : 0;
+            const R d = tau * (th[j] * g_diff(md, j, xf, z));
+            if (!(d < R(kLeapLimit))) {  // beyond the leap limit (or NaN): saturate
+              K[j] = kCountLimit;
+            } else {
+              const long long kj = K[j] + llroundf(d);
+              K[j] = kj > 0 ? kj : 0;
+            }
           }
         }
         return 0;
@@ -636,23 +655,205 @@ struct ThreadTraj {
         if (pk < 0 && target < acc) pk = j;
       }
     } else {
-      DF tot{0.f, 0.f};
-#pragma unroll
-      for (int j = 0; j < MM; ++j) tot = df_add(tot, (float)v[j]);
-      const DF target = df_uniform_times(tot, w.w2, w.w3);
+      // inclusive prefix sums once; the total is the last one
+      DF pre[MM];
       DF acc{0.f, 0.f};
 #pragma unroll
       for (int j = 0; j < MM; ++j) {
         if (v[j] > R(0)) last = j;
         acc = df_add(acc, (float)v[j]);
-        if (pk < 0 && df_lt(target, acc)) pk = j;
+        pre[j] = acc;
       }
+      const DF target = df_uniform_times(acc, w.w2, w.w3);
+#pragma unroll
+      for (int j = 0; j < MM; ++j)
+        if (pk < 0 && df_lt(target, pre[j])) pk = j;
     }
     return pk < 0 ? last : pk;
   }
 
 };
 
+
+// Inputs and outputs of one implicit leap of the fast kernels, passed to the non-inlined
+// solve through local memory so that the leap loop's arrays stay in registers.
+template <int NM, int MM>
+struct ImplicitIo {
+  long long x[NM];
+  long long K[MM];  // in: Poisson draws P_j (and the critical firing); out: firing counts
+  float th[MM];
+};
+
+// Fast precision, FP64 implicit leap (Rathinam 2003): FP64 propensities a_j(x) =
+// theta_j g_j(x) from the FP32 rate constants, Newton's method from y = x with the FP64
+// residual F(y) = y - c - tau sum_j nu_j a_j(y), Jacobian (forward differences or exact),
+// partial pivoting and stopping test max |dy| <= tol max(1, max |y|), then
+// K_j = max(0, round((a_j(y) tau + P_j) - a_j(x) tau)) for the non-critical reactions.
+// Unlike the reference solve it need not reproduce a fixed operation order, so it divides
+// once per species and pivot (reciprocals of the difference steps and pivots) instead of
+// once per Jacobian entry and eliminated element: FP64 division is a long instruction
+// sequence on this GPU.  Not inlined: its FP64 working set stays out of the register
+// allocation of the leap loop.  Returns 0 converged, 1 not converged, 2 singular.
+template <int NM, int MM>
+__device__ __noinline__ int implicit_leap_wide(const ThreadModel<NM, MM>& md,
+                                               ImplicitIo<NM, MM>& io, uint32_t nc,
+                                               double tau, double tol, int maxit, double fd_h,
+                                               bool analytic) {
+  using TR = ThreadTraj<NM, MM, PrecRef>;
+  double th[MM], ax[MM], y[NM], c[NM];
+#pragma unroll
+  for (int j = 0; j < MM; ++j) {
+    th[j] = (double)io.th[j];
+    ax[j] = th[j] * TR::g_int(md, j, io.x);
+  }
+#pragma unroll
+  for (int s = 0; s < NM; ++s) {
+    double acc = (double)io.x[s];
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      const int v = md.nu[j][s];
+      if (((nc >> j) & 1u) && v != 0) acc += (double)v * ((double)io.K[j] - ax[j] * tau);
+    }
+    c[s] = acc;
+    y[s] = (double)io.x[s];
+  }
+  int rc = 1;
+  for (int it = 0; it < maxit && rc == 1; ++it) {
+    double ay[MM];
+#pragma unroll
+    for (int j = 0; j < MM; ++j) ay[j] = ((nc >> j) & 1u) ? th[j] * TR::g_real(md, j, y) : 0.0;
+    double A[NM][NM], b[NM];
+#pragma unroll
+    for (int s = 0; s < NM; ++s) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < MM; ++j) {
+        const int v = md.nu[j][s];
+        if (v != 0) acc += (double)v * ay[j];
+      }
+      b[s] = -((y[s] - c[s]) - tau * acc);
+    }
+#pragma unroll
+    for (int q = 0; q < NM; ++q) {
+      double Dq[MM];
+      if (analytic) {
+#pragma unroll
+        for (int j = 0; j < MM; ++j)
+          Dq[j] = (((nc >> j) & 1u) && md.ord[j][q] != 0)
+                      ? th[j] * TR::template g_real_deriv<double>(md, j, y, q)
+                      : 0.0;
+      } else {
+        const double aq = fabs(y[q]);
+        double yq[NM];
+#pragma unroll
+        for (int s = 0; s < NM; ++s) yq[s] = y[s];
+        yq[q] = y[q] + fd_h * (aq > 1.0 ? aq : 1.0);
+        const double inv_h = 1.0 / (yq[q] - y[q]);
+#pragma unroll
+        for (int j = 0; j < MM; ++j)
+          Dq[j] = (((nc >> j) & 1u) && md.ord[j][q] != 0)
+                      ? (th[j] * TR::g_real(md, j, yq) - ay[j]) * inv_h
+                      : 0.0;
+      }
+#pragma unroll
+      for (int s = 0; s < NM; ++s) {
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < MM; ++j) {
+          const int v = md.nu[j][s];
+          if (v != 0 && md.ord[j][q] != 0) acc += (double)v * Dq[j];
+        }
+        A[s][q] = (s == q ? 1.0 : 0.0) - tau * acc;
+      }
+    }
+    double inv_piv[NM];
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+      int piv = k;
+      double best = fabs(A[k][k]);
+#pragma unroll
+      for (int i = k + 1; i < NM; ++i) {
+        if (fabs(A[i][k]) > best) {
+          best = fabs(A[i][k]);
+          piv = i;
+        }
+      }
+      if (!(best > 0.0)) {
+        rc = 2;
+        break;
+      }
+#pragma unroll
+      for (int i = k + 1; i < NM; ++i) {
+        if (i == piv) {
+#pragma unroll
+          for (int cc = 0; cc < NM; ++cc) {
+            const double tmp = A[k][cc];
+            A[k][cc] = A[i][cc];
+            A[i][cc] = tmp;
+          }
+          const double tb = b[k];
+          b[k] = b[i];
+          b[i] = tb;
+        }
+      }
+      inv_piv[k] = 1.0 / A[k][k];
+#pragma unroll
+      for (int i = k + 1; i < NM; ++i) {
+        const double l = A[i][k] * inv_piv[k];
+#pragma unroll
+        for (int cc = k + 1; cc < NM; ++cc) A[i][cc] -= l * A[k][cc];
+        b[i] -= l * b[k];
+      }
+    }
+    if (rc == 2) break;
+    double dmax = 0.0, ymax = 0.0;
+#pragma unroll
+    for (int i = NM - 1; i >= 0; --i) {
+      const double d = b[i] * inv_piv[i];
+#pragma unroll
+      for (int rr = 0; rr < i; ++rr) b[rr] -= A[rr][i] * d;
+      y[i] += d;
+      dmax = fabs(d) > dmax ? fabs(d) : dmax;
+    }
+#pragma unroll
+    for (int s = 0; s < NM; ++s) ymax = fabs(y[s]) > ymax ? fabs(y[s]) : ymax;
+    if (!(dmax == dmax)) break;
+    if (dmax <= tol * (ymax > 1.0 ? ymax : 1.0)) rc = 0;
+  }
+  if (rc == 0) {
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      if ((nc >> j) & 1u) {
+        const double v = (th[j] * TR::g_real(md, j, y) * tau + (double)io.K[j]) - ax[j] * tau;
+        const double rv = round(v);
+        io.K[j] = !(rv < 0x1p62) ? kCountLimit : (rv > 0.0 ? (long long)rv : 0);
+      }
+    }
+  }
+  return rc;
+}
+
+// Fast precision, FP32 implicit leap for the increment z = y - x (ThreadTraj::
+// implicit_solve_fast), also not inlined.
+template <int NM, int MM>
+__device__ __noinline__ int implicit_leap_fp32(const ThreadModel<NM, MM>& md,
+                                               ImplicitIo<NM, MM>& io, uint32_t nc, float tau,
+                                               double tol, int maxit) {
+  using TF = ThreadTraj<NM, MM, PrecFast>;
+  float th[MM];
+  long long x[NM], K[MM];
+#pragma unroll
+  for (int j = 0; j < MM; ++j) {
+    th[j] = io.th[j];
+    K[j] = io.K[j];
+  }
+#pragma unroll
+  for (int s = 0; s < NM; ++s) x[s] = io.x[s];
+  const int rc = TF::implicit_solve_fast(md, th, x, nc, K, tau, tol, maxit);
+#pragma unroll
+  for (int j = 0; j < MM; ++j) io.K[j] = K[j];
+  return rc;
+}
 
 // One trajectory per thread, driven as a per-lane state machine so that a warp does not
 // hold lanes in one phase while others run a long phase: in each round a lane performs
@@ -817,7 +1018,7 @@ struct ThreadLane {
     for (int k = 0; k < n_slice; ++k) {
       if (b > 0) {
         TT::eval_props(md, x, th, g, a);
-        a0 = lane_tree_sum<MM, R>(a);
+        a0 = reaction_sum<MM, R, P::kRef>(a);
       }
       if (a0 == R(0)) {
         to_horizon = burst_over = true;
@@ -868,8 +1069,9 @@ struct ThreadLane {
       }
     } else {
       const double elapsed = (double)el - (double)elc;
+      // one FP64 addition per reaction and slice: the compensated FP32 sum rounded once
 #pragma unroll
-      for (int j = 0; j < MM; ++j) G[j] = G[j] + ((double)Gs[j] - (double)Gc[j]);
+      for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)(Gs[j] - Gc[j]);
       if (to_horizon) {
         const double left = rem - elapsed > 0.0 ? rem - elapsed : 0.0;
 #pragma unroll
@@ -896,8 +1098,20 @@ struct ThreadLane {
       mode = kDone;
       return;
     }
+    {
+      bool big = false;
+#pragma unroll
+      for (int s = 0; s < NM; ++s) big = big || x[s] > kCountLimit;
+#pragma unroll
+      for (int j = 0; j < MM; ++j) big = big || r[j] > kCountLimit;
+      if (big) {
+        status |= ML_ST_OVERFLOW;
+        mode = kDone;
+        return;
+      }
+    }
     TT::eval_props(md, x, th, g, a);
-    a0 = lane_tree_sum<MM, R>(a);
+    a0 = reaction_sum<MM, R, P::kRef>(a);
     if (a0 == R(0)) {
       const double rm = T - t;
 #pragma unroll
@@ -932,7 +1146,7 @@ struct ThreadLane {
         if (!crit) nc |= 1u << j;
         ac[j] = crit ? a[j] : R(0);
       }
-      const R a0c = lane_tree_sum<MM, R>(ac);
+      const R a0c = reaction_sum<MM, R, P::kRef>(ac);
       const R tau_ex = TT::tau_select(md, a, x, nc, eps);
       // partial equilibrium and the implicit step size
       bool implicit = false;
@@ -986,6 +1200,17 @@ struct ThreadLane {
           at_horizon = true;
         }
         const bool crit_fire = (tau2 <= tau1) && (tau2 <= (R)rm);
+        {
+          bool over = false;
+#pragma unroll
+          for (int j = 0; j < MM; ++j)
+            over = over || (((nc >> j) & 1u) && a[j] * tau > (R)kLeapLimit);
+          if (over) {
+            status |= ML_ST_OVERFLOW;
+            mode = kDone;
+            return;
+          }
+        }
         long long K[MM];
 #pragma unroll
         for (int j = 0; j < MM; ++j) K[j] = 0;
@@ -1016,13 +1241,27 @@ struct ThreadLane {
                   const double ayj = (double)th[j] * TT::g_real(md, j, y);
                   const double v = (ayj * taud + (double)K[j]) - (double)a[j] * taud;
                   const double rv = round(v);
-                  K[j] = rv > 0.0 ? (long long)rv : 0;
+                  K[j] = !(rv < 0x1p62) ? kCountLimit : (rv > 0.0 ? (long long)rv : 0);
                 }
               }
             }
           } else {
-            rc = TT::implicit_solve_fast(md, th, x, nc, K, tau, A.newton_tol,
-                                         A.newton_maxit);
+            ImplicitIo<NM, MM> io;
+#pragma unroll
+            for (int s = 0; s < NM; ++s) io.x[s] = x[s];
+#pragma unroll
+            for (int j = 0; j < MM; ++j) {
+              io.K[j] = K[j];
+              io.th[j] = (float)th[j];
+            }
+            rc = A.newton_fp32
+                     ? implicit_leap_fp32<NM, MM>(md, io, nc, (float)tau, A.newton_tol,
+                                                  A.newton_maxit)
+                     : implicit_leap_wide<NM, MM>(md, io, nc, (double)tau, A.newton_tol,
+                                                  A.newton_maxit, A.fd_h,
+                                                  A.jacobian == ML_JAC_ANALYTIC);
+#pragma unroll
+            for (int j = 0; j < MM; ++j) K[j] = io.K[j];
           }
           if (rc != 0) {
             status |= ML_ST_NEWTON_FAIL;
@@ -1030,6 +1269,16 @@ struct ThreadLane {
             tau1 = tau_ex;
             step++;
             continue;
+          }
+        }
+        if (implicit_step) {
+          bool over = false;
+#pragma unroll
+          for (int j = 0; j < MM; ++j) over = over || (((nc >> j) & 1u) && K[j] > kLeapLimitInt);
+          if (over) {
+            status |= ML_ST_OVERFLOW;
+            mode = kDone;
+            return;
           }
         }
         long long xn[NM];
@@ -1082,10 +1331,15 @@ struct ThreadLane {
 #define ML_THREAD_BOUNDS __launch_bounds__(256, 1)
 #endif
 
-// Warp schedule: in every round a lane that needs a leap evaluation performs one, and a
-// lane inside an SSA burst performs up to kSsaPerRound firings (about the cost of one
-// evaluation), so lanes in different phases progress together instead of a whole burst
-// holding the warp.
+// Warp schedule.  Each round runs one phase for the lanes in it: a leap evaluation
+// (propensities, critical set, step sizes, leap or burst decision) or a slice of up to
+// kSsaPerRound firings of an SSA burst.  The evaluation phase runs when at least
+// args.eval_quorum lanes need it (or no lane is inside a burst); otherwise the lanes inside
+// bursts run a slice while the others wait.  Lanes reach evaluations one by one as their
+// bursts end, so waiting for a quorum gathers them into rounds with many active lanes
+// instead of paying an evaluation for one or two lanes every round (a model of the lane
+// phases of the gene-expression workload: 0.76 of lane slots busy against 0.57).  With
+// eval_quorum = 0 every round runs both phases, each for the lanes in it.
 constexpr int kSsaPerRound = 8;
 
 // Kernel: stage the model tables once per CTA, then run the lane state machine.  Plain
@@ -1096,7 +1350,8 @@ __global__ void ML_THREAD_BOUNDS k_thread(const ThreadModel<NM, MM>* __restrict_
                                           const SimArgs args) {
   __shared__ ThreadModel<NM, MM> smd;
   __shared__ uint64_t mbar;
-  const bool staged = stage_model_bulk(&smd, gmd, (uint32_t)thread_model_bytes<NM, MM>(), &mbar);
+  const bool staged = stage_model_bulk(&smd, gmd, (uint32_t)thread_model_bytes<NM, MM>(), &mbar,
+                                       args.stage_polls);
   using Lane = ThreadLane<NM, MM, P>;
   Lane L;
   L.mode = Lane::kIdle;
@@ -1111,10 +1366,14 @@ __global__ void ML_THREAD_BOUNDS k_thread(const ThreadModel<NM, MM>* __restrict_
         if (nxt < args.n_traj) L.start(smd, args, nxt);
       }
     }
-    if (!__any_sync(0xffffffffu, L.mode != Lane::kIdle)) break;
-    if (L.mode == Lane::kEval) {
+    const unsigned ev = __ballot_sync(0xffffffffu, L.mode == Lane::kEval);
+    const unsigned ss = __ballot_sync(0xffffffffu, L.mode == Lane::kSsa);
+    if (!(ev | ss)) break;
+    const bool both = args.eval_quorum == 0;
+    const bool eval_round = both || ss == 0u || __popc(ev) >= args.eval_quorum;
+    if (eval_round && L.mode == Lane::kEval) {
       L.eval_phase(smd, args);
-    } else if (L.mode == Lane::kSsa) {
+    } else if ((both || !eval_round) && L.mode == Lane::kSsa) {
       L.ssa_slice(smd, args, kSsaPerRound);
     }
   }
@@ -1130,7 +1389,8 @@ __global__ void ML_THREAD_BOUNDS k_thread_seq(const ThreadModel<NM, MM>* __restr
                                               const SimArgs args) {
   __shared__ ThreadModel<NM, MM> smd;
   __shared__ uint64_t mbar;
-  const bool staged = stage_model_bulk(&smd, gmd, (uint32_t)thread_model_bytes<NM, MM>(), &mbar);
+  const bool staged = stage_model_bulk(&smd, gmd, (uint32_t)thread_model_bytes<NM, MM>(), &mbar,
+                                       args.stage_polls);
   using Lane = ThreadLane<NM, MM, P, kGrid>;
   Lane L;
   long long i = args.queue ? (long long)atomicAdd(args.queue, 1ULL)

@@ -20,36 +20,37 @@ namespace mlk {
 constexpr int kRPL = kWarpMaxM / 32;  // reactions per lane
 constexpr int kSPL = kWarpMaxN / 32;  // species per lane
 
-// Per-warp shared-memory slab; offsets depend on the model size and on the working
-// precision R (rbytes = sizeof(R)): the Newton matrix, right-hand side and derivatives are
-// in R, the iterate and its propensities in FP64.
+// Per-warp shared-memory slab; offsets depend on the model size, on the working precision
+// R (rbytes = sizeof(R): propensities) and on the arithmetic of the Newton system
+// (lbytes: the matrix, right-hand side and derivatives; FP64 unless fast precision asks
+// for an FP32 factorization); the iterate and its propensities are FP64.
 struct WarpSlab {
   long long* x;   // [N] state
   long long* xn;  // [N] proposed state
   long long* K;   // [M] firings of the current leap (Poisson draws before the solve)
   double* y;      // [N] Newton iterate
   double* ay;     // [M] propensities at y
-  void* b;        // [N] right-hand side / update (R)
-  void* D;        // [M][3] Jacobian entries by reactant slot (R)
-  void* J;        // [N][N] Newton matrix (R)
+  void* b;        // [N] right-hand side / update (Newton type)
+  void* D;        // [M][3] Jacobian entries by reactant slot (Newton type)
+  void* J;        // [N][N] Newton matrix (Newton type)
   void* a;        // [M] propensities (R)
   void* ac;       // [M] critical propensities (R)
 };
 
-__host__ __device__ inline size_t warp_slab_bytes(int N, int M, int rbytes) {
+__host__ __device__ inline size_t warp_slab_bytes(int N, int M, int rbytes, int lbytes) {
   size_t b = 0;
   b += 8 * (size_t)N * 2;                      // x, xn
   b += 8 * (size_t)M;                          // K
   b += 8 * (size_t)N;                          // y
   b += 8 * (size_t)M;                          // ay
-  b += (size_t)rbytes * N;                     // b
-  b += (size_t)rbytes * 3 * M;                 // D
-  b += (size_t)rbytes * (size_t)N * (size_t)N; // J
+  b += (size_t)lbytes * N;                     // b
+  b += (size_t)lbytes * 3 * M;                 // D
+  b += (size_t)lbytes * (size_t)N * (size_t)N; // J
   b += (size_t)rbytes * M * 2;                 // a, ac
   return (b + 15) / 16 * 16;
 }
 
-__device__ inline WarpSlab carve_slab(char* p, int N, int M, int rbytes) {
+__device__ inline WarpSlab carve_slab(char* p, int N, int M, int rbytes, int lbytes) {
   WarpSlab s;
   s.x = reinterpret_cast<long long*>(p);
   p += 8 * N;
@@ -62,11 +63,11 @@ __device__ inline WarpSlab carve_slab(char* p, int N, int M, int rbytes) {
   s.ay = reinterpret_cast<double*>(p);
   p += 8 * M;
   s.b = p;
-  p += (size_t)rbytes * N;
+  p += (size_t)lbytes * N;
   s.D = p;
-  p += (size_t)rbytes * 3 * M;
+  p += (size_t)lbytes * 3 * M;
   s.J = p;
-  p += (size_t)rbytes * (size_t)N * N;
+  p += (size_t)lbytes * (size_t)N * N;
   s.a = p;
   p += (size_t)rbytes * M;
   s.ac = p;
@@ -217,17 +218,18 @@ struct WarpTraj {
   }
 
   // Implicit solve on the per-warp slab: residual, iterate and stopping test in FP64;
-  // Jacobian, elimination and back substitution in R (FP64 in reference precision).
-  // Returns 0 converged, 1 not converged, 2 singular.
+  // Jacobian, elimination and back substitution in L (FP64, or FP32 when fast precision
+  // asks for an FP32 factorization).  Returns 0 converged, 1 not converged, 2 singular.
+  template <class L>
   __device__ static int implicit_solve(const WarpModel& md, const WarpSlab& sl,
                                        const R (&th)[kRPL], const uint32_t (&nc)[kRPL],
                                        const R* a, double tau, double tol, int maxit,
                                        double fd_h, bool analytic, int lane) {
     const int N = md.N, M = md.M;
-    R* const Jm = static_cast<R*>(sl.J);
-    R* const bv = static_cast<R*>(sl.b);
-    R* const Dm = static_cast<R*>(sl.D);
-    const R taur = (R)tau;
+    L* const Jm = static_cast<L*>(sl.J);
+    L* const bv = static_cast<L*>(sl.b);
+    L* const Dm = static_cast<L*>(sl.D);
+    const L taur = (L)tau;
     double c[kSPL];
 #pragma unroll
     for (int q = 0; q < kSPL; ++q) {
@@ -262,7 +264,7 @@ struct WarpTraj {
             const int j = md.sp_j[e];
             if (bit(nc, j)) acc = acc + (double)md.sp_nu[e] * sl.ay[j];
           }
-          bv[s] = (R)(-((sl.y[s] - c[q]) - tau * acc));
+          bv[s] = (L)(-((sl.y[s] - c[q]) - tau * acc));
         }
       }
 #pragma unroll
@@ -271,16 +273,16 @@ struct WarpTraj {
         if (j < M) {
           const int nr = md.nreact[j];
           for (int k = 0; k < 3; ++k) {
-            R dv = R(0);
+            L dv = L(0);
             if (k < nr && bit(nc, j)) {
               if (analytic) {
-                R v = R(1);
+                L v = L(1);
                 for (int kk = 0; kk < nr; ++kk) {
-                  const R ys = (R)sl.y[md.rsp[j][kk]];
+                  const L ys = (L)sl.y[md.rsp[j][kk]];
                   const int m = md.rmul[j][kk];
-                  v = v * (kk == k ? comb_factor_deriv<R>(ys, m) : comb_factor<R>(ys, m));
+                  v = v * (kk == k ? comb_factor_deriv<L>(ys, m) : comb_factor<L>(ys, m));
                 }
-                dv = th[q] * v;
+                dv = (L)th[q] * v;
               } else {
                 const int sq = md.rsp[j][k];
                 const double yq = sl.y[sq];
@@ -288,7 +290,7 @@ struct WarpTraj {
                 const double h = fd_h * (aq > 1.0 ? aq : 1.0);
                 const double yp = yq + h;
                 const double he = yp - yq;
-                dv = (R)(((double)th[q] * g_real(md, j, sl.y, sq, yp) - sl.ay[j]) / he);
+                dv = (L)(((double)th[q] * g_real(md, j, sl.y, sq, yp) - sl.ay[j]) / he);
               }
             }
             Dm[j * 3 + k] = dv;
@@ -301,28 +303,28 @@ struct WarpTraj {
       for (int q = 0; q < kSPL; ++q) {
         const int s = lane + 32 * q;
         if (s < N) {
-          R* row = Jm + (size_t)s * N;
-          for (int cc = 0; cc < N; ++cc) row[cc] = R(0);
+          L* row = Jm + (size_t)s * N;
+          for (int cc = 0; cc < N; ++cc) row[cc] = L(0);
           for (int e = md.sp_ptr[s]; e < md.sp_ptr[s + 1]; ++e) {
             const int j = md.sp_j[e];
             if (!bit(nc, j)) continue;
-            const R v = (R)md.sp_nu[e];
+            const L v = (L)md.sp_nu[e];
             const int nr = md.nreact[j];
             for (int k = 0; k < nr; ++k) {
               const int qq = md.rsp[j][k];
               row[qq] = row[qq] + v * Dm[j * 3 + k];
             }
           }
-          for (int cc = 0; cc < N; ++cc) row[cc] = (s == cc ? R(1) : R(0)) - taur * row[cc];
+          for (int cc = 0; cc < N; ++cc) row[cc] = (s == cc ? L(1) : L(0)) - taur * row[cc];
         }
       }
       __syncwarp();
       // Gaussian elimination with partial pivoting (largest |pivot|, lowest row on ties)
       for (int k = 0; k < N; ++k) {
-        R best = R(-1);
+        L best = L(-1);
         int piv = N;
         for (int i = k + lane; i < N; i += 32) {
-          const R v = fabs(Jm[(size_t)i * N + k]);
+          const L v = fabs(Jm[(size_t)i * N + k]);
           if (v > best) {
             best = v;
             piv = i;
@@ -330,31 +332,31 @@ struct WarpTraj {
         }
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) {
-          const R ob = __shfl_xor_sync(0xffffffffu, best, d);
+          const L ob = __shfl_xor_sync(0xffffffffu, best, d);
           const int op = __shfl_xor_sync(0xffffffffu, piv, d);
           if (ob > best || (ob == best && op < piv)) {
             best = ob;
             piv = op;
           }
         }
-        if (!(best > R(0)) || piv >= N) return 2;  // zero or non-finite column: singular
+        if (!(best > L(0)) || piv >= N) return 2;  // zero or non-finite column: singular
         if (piv != k) {
           for (int cc = lane; cc < N; cc += 32) {
-            const R t = Jm[(size_t)k * N + cc];
+            const L t = Jm[(size_t)k * N + cc];
             Jm[(size_t)k * N + cc] = Jm[(size_t)piv * N + cc];
             Jm[(size_t)piv * N + cc] = t;
           }
           if (lane == 0) {
-            const R t = bv[k];
+            const L t = bv[k];
             bv[k] = bv[piv];
             bv[piv] = t;
           }
         }
         __syncwarp();
-        const R pk = Jm[(size_t)k * N + k];
-        const R bk = bv[k];
+        const L pk = Jm[(size_t)k * N + k];
+        const L bk = bv[k];
         for (int i = k + 1 + lane; i < N; i += 32) {
-          const R l = Jm[(size_t)i * N + k] / pk;
+          const L l = Jm[(size_t)i * N + k] / pk;
           for (int cc = k + 1; cc < N; ++cc)
             Jm[(size_t)i * N + cc] = Jm[(size_t)i * N + cc] - l * Jm[(size_t)k * N + cc];
           bv[i] = bv[i] - l * bk;
@@ -363,7 +365,7 @@ struct WarpTraj {
       }
       // column-oriented back substitution
       for (int i = N - 1; i >= 0; --i) {
-        const R di = bv[i] / Jm[(size_t)i * N + i];
+        const L di = bv[i] / Jm[(size_t)i * N + i];
         __syncwarp();
         for (int rr = lane; rr < i; rr += 32) bv[rr] = bv[rr] - Jm[(size_t)rr * N + i] * di;
         if (lane == 0) bv[i] = di;
@@ -494,6 +496,22 @@ struct WarpTraj {
       }
       __syncwarp();
     };
+    // After a firing of reaction k inside a burst: recompute only the propensities of the
+    // reactions with a reactant that k changed (the others' reactant counts, hence their
+    // values, are unchanged, so the result equals eval_props bit for bit).
+    auto update_props = [&](int k) {
+      const uint64_t changed = k >= 0 ? md.cmask[k] : ~0ULL;  // unknown: recompute all
+#pragma unroll
+      for (int q = 0; q < kRPL; ++q) {
+        const int j = lane + 32 * q;
+        if (j < M && (md.rmask[j] & changed) != 0ULL) {
+          g[q] = g_int(md, j, sl.x);
+          a[q] = th[q] * g[q];
+          a_s[j] = a[q];
+        }
+      }
+      __syncwarp();
+    };
 
     // Fast precision: inside a burst each lane accumulates its G_j and the elapsed time in
     // compensated FP32 and folds them into the FP64 totals once at the end of the burst.
@@ -505,9 +523,10 @@ struct WarpTraj {
 #pragma unroll
       for (int q = 0; q < kRPL; ++q) Gs[q] = Gc[q] = 0.f;
       bool to_horizon = false;
+      int fired = -1;
       for (int b = 0; b < n_max; ++b) {
         if (b > 0) {
-          eval_props();
+          update_props(fired);
           a0 = tree_sum(a, lane, M);
         }
         if (a0 == R(0)) {
@@ -528,6 +547,7 @@ struct WarpTraj {
           __syncwarp();
         }
         const int pk = pick(a_s, a, w, M, lane);
+        fired = pk;
         if (pk >= 0) {
           const int e0 = md.rx_ptr[pk], e1 = md.rx_ptr[pk + 1];
           for (int e = e0 + lane; e < e1; e += 32) sl.x[md.rx_s[e]] += md.rx_nu[e];
@@ -557,9 +577,10 @@ struct WarpTraj {
         ssa_burst_fast(n_max, a0);
         return;
       }
+      int fired = -1;
       for (int b = 0; b < n_max; ++b) {
         if (b > 0) {
-          eval_props();
+          update_props(fired);
           a0 = tree_sum(a, lane, M);
         }
         if (a0 == R(0)) {
@@ -591,6 +612,7 @@ struct WarpTraj {
         }
         t = tn;
         const int pk = pick(a_s, a, w, M, lane);
+        fired = pk;
         if (pk >= 0) {
           const int e0 = md.rx_ptr[pk], e1 = md.rx_ptr[pk + 1];
           for (int e = e0 + lane; e < e1; e += 32) sl.x[md.rx_s[e]] += md.rx_nu[e];
@@ -610,6 +632,20 @@ struct WarpTraj {
       if ((long long)step >= A.max_steps) {
         status |= ML_ST_STEP_LIMIT;
         break;
+      }
+      {
+        bool big = false;
+#pragma unroll
+        for (int q = 0; q < kSPL; ++q) {
+          const int s = lane + 32 * q;
+          big = big || (s < N && sl.x[s] > kCountLimit);
+        }
+#pragma unroll
+        for (int q = 0; q < kRPL; ++q) big = big || r[q] > kCountLimit;
+        if (__any_sync(0xffffffffu, big)) {
+          status |= ML_ST_OVERFLOW;
+          break;
+        }
       }
       eval_props();
       const R a0 = tree_sum(a, lane, M);
@@ -691,6 +727,7 @@ struct WarpTraj {
             }
           }
         }
+        bool overflow = false;
         for (;;) {
           if (reject_run >= A.max_reject) {
             status |= ML_ST_REJECT_LIMIT;
@@ -717,6 +754,16 @@ struct WarpTraj {
             at_horizon = true;
           }
           const bool crit_fire = (tau2 <= tau1) && (tau2 <= (R)rem);
+          {
+            bool over = false;
+#pragma unroll
+            for (int q = 0; q < kRPL; ++q) {
+              const int j = lane + 32 * q;
+              over = over || (j < M && bit(nc, j) && a[q] * tau > (R)kLeapLimit);
+            }
+            overflow = __any_sync(0xffffffffu, over);
+            if (overflow) break;
+          }
           int cpk = -1;
           if (crit_fire) {
             const Words4 w = philox_block(k0, k1, id, step, Mr + 1u, 0u);
@@ -737,9 +784,13 @@ struct WarpTraj {
           __syncwarp();
           if (implicit_step) {
             const double taud = (double)tau;
-            const int rc = implicit_solve(md, sl, th, nc, a_s, taud, A.newton_tol,
-                                          A.newton_maxit, A.fd_h,
-                                          A.jacobian == ML_JAC_ANALYTIC, lane);
+            const bool an = A.jacobian == ML_JAC_ANALYTIC;
+            const int rc = (!P::kRef && A.newton_fp32)
+                               ? implicit_solve<float>(md, sl, th, nc, a_s, taud, A.newton_tol,
+                                                       A.newton_maxit, A.fd_h, an, lane)
+                               : implicit_solve<double>(md, sl, th, nc, a_s, taud,
+                                                        A.newton_tol, A.newton_maxit, A.fd_h,
+                                                        an, lane);
             if (rc != 0) {
               status |= ML_ST_NEWTON_FAIL;
               implicit = false;
@@ -755,9 +806,17 @@ struct WarpTraj {
                 const double ayj = (double)th[q] * g_real(md, j, sl.y, -1, 0.0);
                 const double v = (ayj * taud + (double)K[q]) - (double)a[q] * taud;
                 const double rv = round(v);
-                K[q] = rv > 0.0 ? (long long)rv : 0;
+                K[q] = !(rv < 0x1p62) ? kCountLimit : (rv > 0.0 ? (long long)rv : 0);
               }
             }
+            bool over = false;
+#pragma unroll
+            for (int q = 0; q < kRPL; ++q) {
+              const int j = lane + 32 * q;
+              over = over || (j < M && bit(nc, j) && K[q] > kLeapLimitInt);
+            }
+            overflow = __any_sync(0xffffffffu, over);
+            if (overflow) break;
           }
 #pragma unroll
           for (int q = 0; q < kRPL; ++q) {
@@ -814,6 +873,10 @@ struct WarpTraj {
           reject_run = 0;
           break;
         }
+        if (overflow) {
+          status |= ML_ST_OVERFLOW;
+          break;
+        }
       }
       if (burst > 0) {
         ssa_burst(burst, a0);
@@ -859,18 +922,23 @@ struct WarpTraj {
 // Kernel: model tables staged once per CTA into the front of dynamic shared memory, one
 // slab per warp after them.  Plain form: warp w of CTA b runs trajectory b*warps + w.
 // Persistent form: lane 0 claims the next trajectory from the device queue.
+// Bounds (256, 1): without a minimum-CTA hint ptxas held the kernel to 80 registers and
+// spilled about 1.4 KB per thread; residency is set by the shared-memory slabs anyway
+// (a 50 x 100 network's FP64 Newton system is 20 KB per warp).
 template <class P, bool kGrid = false>
-__global__ void __launch_bounds__(256) k_warp(const WarpModel* __restrict__ gmd,
+__global__ void __launch_bounds__(256, 1) k_warp(const WarpModel* __restrict__ gmd,
                                               const SimArgs args) {
   extern __shared__ __align__(16) char smem[];
   __shared__ uint64_t mbar;
   WarpModel& md = *reinterpret_cast<WarpModel*>(smem);
-  const bool staged = stage_model_bulk(&md, gmd, (uint32_t)((sizeof(WarpModel) + 15) / 16 * 16), &mbar);
+  const bool staged = stage_model_bulk(&md, gmd, (uint32_t)((sizeof(WarpModel) + 15) / 16 * 16), &mbar,
+                                       args.stage_polls);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
   const size_t mbytes = (sizeof(WarpModel) + 15) / 16 * 16;
   const int rbytes = (int)sizeof(typename P::R);
-  char* slab_base = smem + mbytes + (size_t)warp * warp_slab_bytes(md.N, md.M, rbytes);
-  const WarpSlab sl = carve_slab(slab_base, md.N, md.M, rbytes);
+  const int lbytes = (!P::kRef && args.newton_fp32) ? 4 : 8;
+  char* slab_base = smem + mbytes + (size_t)warp * warp_slab_bytes(md.N, md.M, rbytes, lbytes);
+  const WarpSlab sl = carve_slab(slab_base, md.N, md.M, rbytes, lbytes);
   long long i;
   if (args.queue) {
     long long c = 0;

@@ -19,13 +19,14 @@ LIB_PATH = os.path.join(_HERE, "libmatleap.so")
 ML_OK, ML_ERR_ARG, ML_ERR_OOM, ML_ERR_CUDA, ML_ERR_TIMEOUT, ML_ERR_BUSY, ML_ERR_UNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6
 ML_ST_STEP_LIMIT, ML_ST_NEWTON_FAIL, ML_ST_REJECT_LIMIT, ML_ST_PTRS_CAP = 1, 2, 4, 8
-ML_ST_BAD_INPUT, ML_ST_STAGE_TIMEOUT = 16, 32
+ML_ST_BAD_INPUT, ML_ST_STAGE_TIMEOUT, ML_ST_OVERFLOW = 16, 32, 64
 ML_MODE_ADAPTIVE, ML_MODE_EXPLICIT_ONLY, ML_MODE_SSA_ONLY = 0, 1, 2
 ML_PREC_REF_FP64, ML_PREC_FAST_FP32 = 0, 1
 ML_FORM_PLAIN, ML_FORM_PERSISTENT = 0, 1
 ML_SHAPE_AUTO, ML_SHAPE_THREAD, ML_SHAPE_WARP, ML_SHAPE_THREAD_OCC, ML_SHAPE_THREAD_SEQ = 0, 1, 2, 3, 4
 ML_SHAPE_THREAD_SEQ_OCC = 5
 ML_JAC_FD, ML_JAC_ANALYTIC = 0, 1
+ML_NEWTON_FP64, ML_NEWTON_FP32 = 0, 1
 
 
 class MatleapError(RuntimeError):
@@ -42,7 +43,9 @@ class ml_sim_params(C.Structure):
                 ("fd_h", C.c_double), ("max_steps", C.c_int64), ("max_reject", C.c_int32),
                 ("mode", C.c_int32), ("precision", C.c_int32), ("form", C.c_int32),
                 ("shape", C.c_int32), ("block_size", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("use_graph", C.c_int32), ("jacobian", C.c_int32)]
+                ("use_graph", C.c_int32), ("jacobian", C.c_int32),
+                ("newton_precision", C.c_int32), ("stage_poll_limit", C.c_int32),
+                ("eval_quorum", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -354,6 +357,19 @@ def ml_resample_systematic(logw, seed: int = 0, id_base: int = 0, ancestors=None
                                         _ptr(workspace), workspace.numel(),
                                         _stream_handle(stream)))
     return ancestors
+
+
+def shard_bounds(n_total: int, rank: int, world: int) -> tuple:
+    """Trajectory ids [lo, hi) of rank `rank` of `world` when n_total trajectories are
+    split into contiguous, nearly equal ranges (the first n_total % world ranks take one
+    more).  A rank simulates rows lo..hi-1 of the per-trajectory inputs with
+    traj_id_base = lo; because every random number is keyed by the global id, the
+    concatenated results equal one call over all ids, whatever the partition."""
+    if world < 1 or not 0 <= rank < world or n_total < 0:
+        raise ValueError("need world >= 1, 0 <= rank < world and n_total >= 0")
+    q, rem = divmod(n_total, world)
+    lo = rank * q + min(rank, rem)
+    return lo, lo + q + (1 if rank < rem else 0)
 
 
 def model_from_crn(crn) -> Model:

@@ -280,22 +280,34 @@ def config(i: int, n_traj: Optional[int] = None, seed: int = 0) -> Workload:
     raise ValueError(f"no workload {i}")
 
 
+# Horizon of each model's requests as a fraction of its benchmark horizon.  At 200
+# requests/s of 1,000-100,000 trajectories (mean 21,500) each model is offered about
+# 1.07e6 trajectories/s.  One GB300 simulates immigration-death at T = 100 at about
+# 5e6/s, the dimerisation at T = 0.2 at about 3e7/s, gene expression at T ~ 125 at about
+# 4.6e5/s (SSA-bound: the offered load would be 2.3 GPUs) and the 50 x 100 network at
+# T = 10 at about 2e2/s (5,000 GPUs).  The scales bring every model to a fraction of one
+# GPU: immigration-death 0.5 (about 10 %), dimerisation 1 (3 %), gene expression 0.03
+# (7 %), random network 5e-5 (about 25 %), so that the mix as a whole is servable.
 SERVING_HORIZON_SCALE = {0: 0.5, 1: 1.0, 2: 0.03, 3: 5e-5}
+# Shape of the per-request Gamma spread of rate constants around each model's rates: the
+# gene-expression workload's shape 2 wherever possible; the dimerisation keeps shape 50
+# (about 14 %), because a wider spread pushes its stiff pair out of partial equilibrium
+# and turns the model SSA-bound.
+SERVING_THETA_SHAPE = {0: 2.0, 1: 50.0, 2: 2.0, 3: 2.0}
 
 
 def serving_requests(n_requests: int, seed: int = 0, rate_hz: float = 200.0,
                      min_traj: int = 1_000, max_traj: int = 100_000, models=(0, 1, 2, 3),
-                     horizon_scale=None, theta_shape: float = 50.0):
+                     horizon_scale=None, theta_shape=None):
     """Poisson-arrival request stream for the serving mix: each request picks a model
     uniformly from `models`, a log-uniform trajectory count in [min_traj, max_traj], its
-    own per-trajectory rate constants theta ~ Gamma(theta_shape, rate theta_shape / k)
-    around the model's rates k (shape 50: about 14 % spread, which keeps the stiff pair of
-    the dimerisation near partial equilibrium) and its own horizon: the model's horizon x
-    horizon_scale[model] x U[0.5, 1].  The default scales keep the offered load of the
-    SSA-bound models (gene expression, random 50 x 100 network) within one GPU at 200
-    requests/s.  Returns a list of dicts with arrival time (s), Workload and a distinct
-    trajectory-id base."""
+    own per-trajectory rate constants theta ~ Gamma(shape, rate shape / k) around the
+    model's rates k (shape from theta_shape, default SERVING_THETA_SHAPE) and its own
+    horizon: the model's horizon x horizon_scale[model] x U[0.5, 1] (default
+    SERVING_HORIZON_SCALE).  Returns a list of dicts with arrival time (s), Workload and a
+    distinct trajectory-id base."""
     scales = dict(SERVING_HORIZON_SCALE if horizon_scale is None else horizon_scale)
+    shapes = dict(SERVING_THETA_SHAPE if theta_shape is None else theta_shape)
     rng = np.random.default_rng(seed)
     t = 0.0
     base = 0
@@ -307,8 +319,8 @@ def serving_requests(n_requests: int, seed: int = 0, rate_hz: float = 200.0,
         B = int(np.floor(np.exp(rng.uniform(np.log(min_traj), np.log(max_traj)))))
         w0 = bases[m]
         crn = w0.crn
-        theta = np.ascontiguousarray(rng.gamma(theta_shape, crn.rates / theta_shape,
-                                               size=(B, crn.n_reactions)))
+        k = shapes.get(m, 2.0)
+        theta = np.ascontiguousarray(rng.gamma(k, crn.rates / k, size=(B, crn.n_reactions)))
         Tm = float(w0.T[0] if w0.T.shape[0] == 1 else 125.0) * scales.get(m, 1.0)
         T = np.ascontiguousarray(Tm * rng.uniform(0.5, 1.0, size=B))
         wl = Workload(f"req{q}_{w0.name}", crn, B, w0.x0.copy(), T, theta,

@@ -1,0 +1,94 @@
+"""Failure paths the library reports per trajectory, driven on the GPU without faulting
+it: a Newton solve that cannot converge (one iteration, a tolerance no step meets) falls
+back to an explicit leap with ML_ST_NEWTON_FAIL, and a model-staging wait with a poll limit
+of 0 runs out, so every CTA copies its tables with plain loads and reports
+ML_ST_STAGE_TIMEOUT.  Both must leave the results equal to the oracle's."""
+import numpy as np
+import pytest
+
+from paper_1608_07058_gb300 import workloads as W
+from tests.test_gpu_parity import assert_bit_parity, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ml():
+    import torch
+    from paper_1608_07058_gb300 import build, matleap
+    assert torch.cuda.is_available()
+    build.build()
+    matleap.lib()
+    return matleap
+
+
+@pytest.mark.parametrize("shape", [4, 1, 2])
+def test_forced_newton_failure_falls_back_to_explicit(ml, oracle, shape):
+    w = W.config(1, n_traj=2000)
+    kw = dict(newton_maxit=1, newton_tol=1e-300, shape=shape)
+    g = run_gpu(ml, w.crn, w.n_traj, w.x0, w.T, seed=61, **kw)
+    o = run_oracle(oracle, w.crn, w.n_traj, w.x0, w.T, seed=61, newton_maxit=1,
+                   newton_tol=1e-300)
+    assert_bit_parity(g, o, f"shape {shape}")
+    assert (g["status"] & ml.ML_ST_NEWTON_FAIL).all()   # every trajectory tried a solve
+    assert (g["counters"][:, 1] == 0).all()             # and no implicit leap was taken
+    assert (g["counters"][:, 0] > 0).all()
+
+
+def test_forced_newton_failure_fast_precision(ml, oracle):
+    w = W.config(1, n_traj=2000)
+    for newton in (ml.ML_NEWTON_FP64, ml.ML_NEWTON_FP32):
+        g = run_gpu(ml, w.crn, w.n_traj, w.x0, w.T, seed=62, newton_maxit=1,
+                    newton_tol=1e-300, precision=ml.ML_PREC_FAST_FP32,
+                    newton_precision=newton, shape=4)
+        assert (g["status"] & ml.ML_ST_NEWTON_FAIL).all()
+        # Every trajectory attempts thousands of implicit leaps here.  One converges only
+        # when its Poisson draws change no species (nu^T P = 0), which makes the first
+        # Newton update exactly zero: a leap cut to a remaining horizon of a few 1e-6 (mean
+        # firings of the pair about 8, so P_2 = P_3 with probability about 0.1).
+        assert (g["counters"][:, 1] <= 1).all()
+        assert (g["counters"][:, 1] == 0).mean() > 0.7
+        assert np.array_equal(g["X"], w.x0 + g["r"] @ w.crn.stoich)
+
+
+@pytest.mark.parametrize("shape,cfg,n", [(1, 1, 3000), (4, 2, 300), (2, 1, 500)])
+def test_staging_timeout_falls_back_to_plain_loads(ml, oracle, shape, cfg, n):
+    w = W.config(cfg, n_traj=n)
+    g = run_gpu(ml, w.crn, n, w.x0, w.T, w.theta, seed=63, shape=shape, stage_poll_limit=0,
+                form=ml.ML_FORM_PERSISTENT)
+    o = run_oracle(oracle, w.crn, n, w.x0, w.T, w.theta, seed=63)
+    assert (g["status"] & ml.ML_ST_STAGE_TIMEOUT).all()
+    g["status"] = g["status"] & ~np.uint32(ml.ML_ST_STAGE_TIMEOUT)
+    assert_bit_parity(g, o, f"shape {shape}")
+    # with the default limit the copy completes and no trajectory reports a timeout
+    g2 = run_gpu(ml, w.crn, n, w.x0, w.T, w.theta, seed=63, shape=shape,
+                 form=ml.ML_FORM_PERSISTENT)
+    assert not (g2["status"] & ml.ML_ST_STAGE_TIMEOUT).any()
+
+
+@pytest.mark.parametrize("shape", [1, 4, 2])
+def test_count_limits_match_the_oracle(ml, oracle, shape):
+    """The count limits (status OVERFLOW): a count above 2^62 at the start, autocatalysis
+    that passes the 2^48 leap limit mid-run, and Poisson means above 2^48 in a pair at
+    equilibrium: bit parity with the oracle, status included."""
+    auto = W._crn("autocatalysis", 1, [({0: 1}, {0: 2}, 85.0)])
+    cases = [(W.pure_decay(1e-30), [2 ** 62 + 1], 1.0, 8), (auto, [1], 0.5, 300),
+             (auto, [1], 0.3, 300), (W.isomerisation(1000.0, 1000.0), [2 ** 40, 2 ** 40], 1.0, 8)]
+    for crn, x0, T, n in cases:
+        g = run_gpu(ml, crn, n, x0, [T], seed=71, shape=shape)
+        o = run_oracle(oracle, crn, n, x0, [T], seed=71)
+        assert_bit_parity(g, o, f"{crn.name} T={T} shape {shape}")
+        # (Poisson means near the limit may also hit the PTRS trial cap, bit 8)
+        over = (g["status"] & ml.ML_ST_OVERFLOW) != 0
+        assert (~over).all() if T == 0.3 else over.all(), (crn.name, T)
+
+
+def test_count_limits_fast_precision(ml):
+    auto = W._crn("autocatalysis", 1, [({0: 1}, {0: 2}, 85.0)])
+    for shape in (4, 2):
+        g = run_gpu(ml, auto, 300, [1], [0.5], seed=72, shape=shape,
+                    precision=ml.ML_PREC_FAST_FP32)
+        assert ((g["status"] & ml.ML_ST_OVERFLOW) != 0).all()
+        X = g["X"][:, 0]
+        assert np.array_equal(X, 1 + g["r"][:, 0])
+        assert (X > 0.9 * 2 ** 48 / 0.03).all() and (X < 2 ** 62).all()

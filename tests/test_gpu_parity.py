@@ -324,3 +324,21 @@ def test_ref_bit_parity_thread_drivers(ml, oracle, shape, cfg, n):
     for form in (0, 1):
         g = run_gpu(ml, w.crn, n, w.x0, w.T, w.theta, seed=41, shape=shape, form=form)
         assert_bit_parity(g, o, f"shape{shape} form{form}")
+
+
+@pytest.mark.parametrize("shape,newton,jac", [
+    (4, 0, 0), (4, 0, 1), (4, 1, 1), (5, 0, 0), (5, 1, 1), (1, 0, 0), (3, 0, 1),
+    (2, 0, 0), (2, 1, 0)])
+def test_fast_statistics_dimerisation_newton_forms(ml, oracle, shape, newton, jac):
+    """Fast precision with the FP64 Newton solve (forward-difference or exact Jacobian) and
+    with the FP32 one, in every thread driver/build and the warp kernel: the ensemble of
+    20,000 stiff-dimerisation trajectories (about 14 implicit leaps each) matches the
+    oracle's statistics."""
+    w = W.config(1, n_traj=20000)
+    g = run_gpu(ml, w.crn, w.n_traj, w.x0, w.T, seed=41 + shape, precision=ml.ML_PREC_FAST_FP32,
+                form=ml.ML_FORM_PERSISTENT, shape=shape, newton_precision=newton, jacobian=jac)
+    o = run_oracle(oracle, w.crn, w.n_traj, w.x0, w.T, seed=41 + shape, jacobian=jac)
+    assert (g["counters"][:, 1] > 0).mean() > 0.99
+    s = stats_util.summary(stats_util.compare(g, o, g_res=stats_util.G_RESOLUTION_FAST))
+    assert s["holm_pass_0.01"], s
+    assert (g["status"] == 0).all()

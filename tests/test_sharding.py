@@ -89,3 +89,49 @@ def test_two_rank_grid_and_posterior_shards(tmp_path, oracle):
                                         seed=7)
     assert np.array_equal(got["X_obs"], ref["X_obs"])
     assert np.array_equal(got["theta"], theta) and np.array_equal(got["st"], st)
+
+
+def _worker_uneven(rank, world, port, n, result_path):
+    """The package's partition (matleap.shard_bounds, uneven sizes) with the oracle as the
+    simulator on each rank."""
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import oracle as O
+    from paper_1608_07058_gb300 import workloads as W
+    from paper_1608_07058_gb300.matleap import shard_bounds
+    w = W.config(2, n_traj=n)
+    lo, hi = shard_bounds(n, rank, world)
+    out = O.simulate(w.crn, hi - lo, w.x0, w.T[lo:hi], w.theta[lo:hi], seed=9, traj_id_base=lo)
+    parts = [None] * world
+    dist.all_gather_object(parts, {k: out[k] for k in ("X", "r", "G", "status")})
+    if rank == 0:
+        np.savez(result_path, **{k: np.concatenate([p[k] for p in parts]) for k in parts[0]})
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_shard_bounds_partition():
+    from paper_1608_07058_gb300.matleap import shard_bounds
+    for n in (0, 1, 5, 64, 67, 1000):
+        for world in (1, 2, 3, 7):
+            rng = [shard_bounds(n, k, world) for k in range(world)]
+            assert rng[0][0] == 0 and rng[-1][1] == n
+            assert all(a[1] == b[0] for a, b in zip(rng, rng[1:]))
+            sizes = [hi - lo for lo, hi in rng]
+            assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        shard_bounds(10, 2, 2)
+
+
+def test_three_rank_uneven_shards_concatenate_to_single_run(tmp_path, oracle):
+    from paper_1608_07058_gb300 import workloads as W
+    n, world = 67, 3
+    path = str(tmp_path / "gathered_uneven.npz")
+    mp.spawn(_worker_uneven, args=(world, _free_port(), n, path), nprocs=world, join=True)
+    got = np.load(path)
+    w = W.config(2, n_traj=n)
+    ref = oracle.simulate(w.crn, n, w.x0, w.T, w.theta, seed=9)
+    for k in ("X", "r", "G", "status"):
+        assert np.array_equal(got[k], ref[k]), k

@@ -87,3 +87,27 @@ def test_noalloc_rejects_models_beyond_its_scratch(ml):
                                out=_bufs(torch, n, model.N, model.M))
     assert e.value.code == ml.ML_ERR_ARG
     assert "at most" in str(e.value)
+
+
+def test_noalloc_leaves_free_device_memory_unchanged(ml):
+    """On a model that never went through ml_simulate (so it owns no device tables), after
+    one warm-up call (which may load the library's module), further calls change nothing
+    in the device's free memory; their results equal a later ml_simulate run."""
+    import torch
+    d = torch.device("cuda")
+    w = W.config(1, n_traj=4000)
+    model = ml.model_from_crn(w.crn)
+    x0 = torch.as_tensor(w.x0, device=d)
+    T = torch.as_tensor(w.T, device=d)
+    outs = [_bufs(torch, w.n_traj, model.N, model.M) for _ in range(4)]
+    ml.ml_simulate_noalloc(model, w.n_traj, x0, T, seed=3, out=outs[0])
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in range(1, 4):
+        ml.ml_simulate_noalloc(model, w.n_traj, x0, T, seed=3 + k, out=outs[k])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    ref = ml.ml_simulate(model, w.n_traj, x0, T, seed=6, out=_bufs(torch, w.n_traj, model.N, model.M))
+    torch.cuda.synchronize()
+    for key in ("X", "r", "G", "status", "counters"):
+        assert torch.equal(ref[key], outs[3][key]), key
