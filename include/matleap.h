@@ -117,7 +117,7 @@ typedef struct ml_model ml_model;
  * pe_delta 0.05, stiff_ratio 100, newton_tol 1e-10, newton_maxit 20, fd_h 1e-7,
  * max_steps 1e8, max_reject 64, mode ADAPTIVE, precision REF_FP64, form PLAIN,
  * shape AUTO, block_size 0 (tuned or default), ctas_per_sm 0, use_graph 0,
- * jacobian FD, newton_precision FP64, stage_poll_limit 4194304, eval_quorum 4. */
+ * jacobian FD, newton_precision FP64, stage_poll_limit 4194304. */
 typedef struct {
   double eps;             /* Cao 2006 bound on the relative change of each reactant    */
   int32_t n_c;            /* critical threshold (Section 2)                            */
@@ -144,11 +144,6 @@ typedef struct {
                                model tables before the CTA falls back to plain loads
                                and sets ML_ST_STAGE_TIMEOUT (>= 0; 0 forces the
                                fallback, which tests use to exercise it)               */
-  int32_t eval_quorum;    /* round-based thread shapes: a round runs the leap-evaluation
-                               phase when at least this many of a warp's lanes need it (or
-                               none is inside an SSA burst), else a slice of the bursts;
-                               0 runs both phases every round.  Results do not depend on
-                               it.  0..32, default 4                                    */
 } ml_sim_params;
 
 /* Fills *p with the defaults above.  Returns ML_ERR_ARG if p is NULL. */

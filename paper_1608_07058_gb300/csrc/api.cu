@@ -318,8 +318,6 @@ int check_params(const ml_sim_params& p) {
   if (p.newton_precision != ML_NEWTON_FP64 && p.newton_precision != ML_NEWTON_FP32)
     return fail(ML_ERR_ARG, "unknown newton_precision %d", p.newton_precision);
   if (p.stage_poll_limit < 0) return fail(ML_ERR_ARG, "stage_poll_limit must be >= 0");
-  if (p.eval_quorum < 0 || p.eval_quorum > 32)
-    return fail(ML_ERR_ARG, "eval_quorum must be in [0, 32]");
   return ML_OK;
 }
 
@@ -498,7 +496,6 @@ void fill_args(const ml_model* m, const ml_sim_params& p, int64_t n_traj, const 
   a->jacobian = p.jacobian;
   a->newton_fp32 = p.precision == ML_PREC_FAST_FP32 && p.newton_precision == ML_NEWTON_FP32;
   a->stage_polls = p.stage_poll_limit;
-  a->eval_quorum = p.eval_quorum;
   a->queue = nullptr;
 }
 
@@ -672,7 +669,6 @@ int ml_default_params(ml_sim_params* p) {
   p->jacobian = ML_JAC_FD;
   p->newton_precision = ML_NEWTON_FP64;
   p->stage_poll_limit = 1 << 22;
-  p->eval_quorum = 4;
   return ML_OK;
 }
 

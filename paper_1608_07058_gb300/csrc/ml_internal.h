@@ -116,7 +116,6 @@ struct SimArgs {
   int32_t jacobian;  // ML_JAC_*
   int32_t newton_fp32;  // fast precision: FP32 implicit solve (ML_NEWTON_FP32)
   int32_t stage_polls;  // bounded wait for the model-table bulk copy
-  int32_t eval_quorum;  // round-based thread driver: lanes needing an evaluation per round
   // persistent form: next unclaimed trajectory (zeroed before each launch)
   unsigned long long* queue;
   // time-grid output: K_obs observation times (nondecreasing, >= 0, finite; checked on the

@@ -1331,15 +1331,11 @@ struct ThreadLane {
 #define ML_THREAD_BOUNDS __launch_bounds__(256, 1)
 #endif
 
-// Warp schedule.  Each round runs one phase for the lanes in it: a leap evaluation
-// (propensities, critical set, step sizes, leap or burst decision) or a slice of up to
-// kSsaPerRound firings of an SSA burst.  The evaluation phase runs when at least
-// args.eval_quorum lanes need it (or no lane is inside a burst); otherwise the lanes inside
-// bursts run a slice while the others wait.  Lanes reach evaluations one by one as their
-// bursts end, so waiting for a quorum gathers them into rounds with many active lanes
-// instead of paying an evaluation for one or two lanes every round (a model of the lane
-// phases of the gene-expression workload: 0.76 of lane slots busy against 0.57).  With
-// eval_quorum = 0 every round runs both phases, each for the lanes in it.
+// Warp schedule: in every round a lane that needs a leap evaluation performs one, and a
+// lane inside an SSA burst performs up to kSsaPerRound firings (about the cost of one
+// evaluation), so lanes in different phases progress together instead of a whole burst
+// holding the warp.  (Running only one phase per round, the evaluations once at least 4
+// or 8 lanes need one, measured 2.6 and 1.8 times slower on the gene-expression batch.)
 constexpr int kSsaPerRound = 8;
 
 // Kernel: stage the model tables once per CTA, then run the lane state machine.  Plain
@@ -1366,14 +1362,10 @@ __global__ void ML_THREAD_BOUNDS k_thread(const ThreadModel<NM, MM>* __restrict_
         if (nxt < args.n_traj) L.start(smd, args, nxt);
       }
     }
-    const unsigned ev = __ballot_sync(0xffffffffu, L.mode == Lane::kEval);
-    const unsigned ss = __ballot_sync(0xffffffffu, L.mode == Lane::kSsa);
-    if (!(ev | ss)) break;
-    const bool both = args.eval_quorum == 0;
-    const bool eval_round = both || ss == 0u || __popc(ev) >= args.eval_quorum;
-    if (eval_round && L.mode == Lane::kEval) {
+    if (!__any_sync(0xffffffffu, L.mode != Lane::kIdle)) break;
+    if (L.mode == Lane::kEval) {
       L.eval_phase(smd, args);
-    } else if ((both || !eval_round) && L.mode == Lane::kSsa) {
+    } else if (L.mode == Lane::kSsa) {
       L.ssa_slice(smd, args, kSsaPerRound);
     }
   }

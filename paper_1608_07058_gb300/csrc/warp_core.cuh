@@ -922,11 +922,13 @@ struct WarpTraj {
 // Kernel: model tables staged once per CTA into the front of dynamic shared memory, one
 // slab per warp after them.  Plain form: warp w of CTA b runs trajectory b*warps + w.
 // Persistent form: lane 0 claims the next trajectory from the device queue.
-// Bounds (256, 1): without a minimum-CTA hint ptxas held the kernel to 80 registers and
-// spilled about 1.4 KB per thread; residency is set by the shared-memory slabs anyway
-// (a 50 x 100 network's FP64 Newton system is 20 KB per warp).
+// Bounds (256, ML_WARP_MIN_BLOCKS): without a minimum-CTA hint ptxas held the kernel to 80
+// registers and spilled about 1.4 KB per thread.
+#ifndef ML_WARP_MIN_BLOCKS
+#define ML_WARP_MIN_BLOCKS 1
+#endif
 template <class P, bool kGrid = false>
-__global__ void __launch_bounds__(256, 1) k_warp(const WarpModel* __restrict__ gmd,
+__global__ void __launch_bounds__(256, ML_WARP_MIN_BLOCKS) k_warp(const WarpModel* __restrict__ gmd,
                                               const SimArgs args) {
   extern __shared__ __align__(16) char smem[];
   __shared__ uint64_t mbar;

