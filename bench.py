@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--extra-configs", default="1",
                     help="comma-separated workloads measured beside the headline")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-order", action="store_true",
+                    help="hand trajectories out in index order (no longest-first queue order)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default launch shape (for very long workloads)")
@@ -534,17 +536,26 @@ class Bench:
                 "counters": torch.empty((B, 4), dtype=torch.int64, device=d)}
 
     def timed(self, model, B, x0, T, theta, params, seed0, id_base, steps, warmup,
-                      budget_s=None, min_steps=2):
+                      budget_s=None, min_steps=2, order_from_warmup=False):
         """`warmup` full untimed steps (or, with warmup = 0, one launch on a 4,096-trajectory
         prefix), then timed steps: `steps` of them, or fewer once budget_s seconds of timed
         work have passed (never fewer than min_steps).  L2 is flushed before every step;
-        each step is bracketed by CUDA events on the launching stream."""
+        each step is bracketed by CUDA events on the launching stream.  With
+        order_from_warmup the timed steps hand trajectories out longest first, by the last
+        warm-up step's per-trajectory event counts (an implicit or explicit leap counted as 8
+        SSA firings); the order is computed once, before timing."""
         import torch
         ml, stream = self.ml, self.stream
         out = self.outputs(model, B)
         for s in range(warmup):
             ml.ml_simulate(model, B, x0, T, theta, params=params, seed=seed0 + s,
                            traj_id_base=id_base, out=out)
+        if order_from_warmup and warmup > 0:
+            c = out["counters"]
+            cost = 8 * (c[:, 0] + c[:, 1]) + c[:, 2] + c[:, 3]
+            self.order = torch.argsort(cost, descending=True, stable=True).to(torch.int64).contiguous()
+            self.order_host = self.order.cpu().pin_memory()
+            params.queue_order = self.order.data_ptr()
         if warmup == 0:
             n0 = min(B, 4096)
             ml.ml_simulate(model, n0, x0 if x0.dim() == 1 else x0[:n0],
@@ -663,7 +674,7 @@ def run_ours(args):
     if not args.ncu:
         clocks.start()
     res_fast = bench.timed(model, B, x0, T, theta, fast, 1000, id_base, args.steps,
-                                   args.warmup)
+                           args.warmup, order_from_warmup=not args.no_order)
     clk = clocks.stop() if not args.ncu else None
     ms_fast = max_over_ranks(res_fast["mean_ms"])
     counts_fast = sum_over_ranks(res_fast["counts"].astype(np.float64)) / res_fast["steps"]
@@ -677,6 +688,9 @@ def run_ours(args):
                        "form": "persistent refill kernel, CUDA graph, autotuned",
                        "precision": precision_label(ml, fast),
                        "jacobian": args.jacobian, "shape": shape_of(fast),
+                       "queue_order": "longest first by the last warm-up step's per-trajectory "
+                                      "event counts (computed once, before timing)"
+                                      if fast.queue_order else "trajectory index",
                        "l2": "flushed between steps (256 MB write)"},
             "leap_steps_per_s": leap_steps / (ms_fast / 1e3),
             "accepted_leaps_per_s": float(counts_fast[0] + counts_fast[1]) / (ms_fast / 1e3),
@@ -743,6 +757,8 @@ def run_ours(args):
                 "G": torch.empty((B, model.M), dtype=torch.float64).pin_memory(),
                 "status": torch.empty((B,), dtype=torch.int32).pin_memory(),
                 "counters": torch.empty((B, 4), dtype=torch.int64).pin_memory()}
+        if fast.queue_order:  # the host entry point takes the order in host memory
+            fast.queue_order = bench.order_host.data_ptr()
         ml.ml_simulate_host(model, B, hx0, hT, hth, params=fast, seed=99, traj_id_base=id_base,
                             out=hout, stream=stream)
         barrier()
@@ -761,7 +777,11 @@ def run_ours(args):
         line["e2e"] = {"value": world * B / e2e_s, "unit": "trajectories/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                        "steps": k, "warmup": 1,
-                       "path": "ml_simulate_host: pinned host inputs -> device -> simulate -> host"}
+                       "path": "ml_simulate_host: pinned host inputs (and the queue order) -> "
+                               "device -> simulate -> host"}
+        if fast.queue_order:
+            line["e2e"]["h2d_bytes_per_step"] += B * 8
+            fast.queue_order = bench.order.data_ptr()
 
     # CPU oracle baseline and oracle-matched statistics (rank 0, N = 1 only for the baseline)
     if rank == 0 and not args.no_cpu and not args.ncu:

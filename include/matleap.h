@@ -117,7 +117,7 @@ typedef struct ml_model ml_model;
  * pe_delta 0.05, stiff_ratio 100, newton_tol 1e-10, newton_maxit 20, fd_h 1e-7,
  * max_steps 1e8, max_reject 64, mode ADAPTIVE, precision REF_FP64, form PLAIN,
  * shape AUTO, block_size 0 (tuned or default), ctas_per_sm 0, use_graph 0,
- * jacobian FD, newton_precision FP64, stage_poll_limit 4194304. */
+ * jacobian FD, newton_precision FP64, stage_poll_limit 4194304, queue_order NULL. */
 typedef struct {
   double eps;             /* Cao 2006 bound on the relative change of each reactant    */
   int32_t n_c;            /* critical threshold (Section 2)                            */
@@ -144,6 +144,17 @@ typedef struct {
                                model tables before the CTA falls back to plain loads
                                and sets ML_ST_STAGE_TIMEOUT (>= 0; 0 forces the
                                fallback, which tests use to exercise it)               */
+  const int64_t* queue_order; /* persistent form: NULL, or [n_traj] int64, a permutation of
+                               0..n_traj-1: the work queue hands trajectories out in this
+                               order.  Giving the longest first removes the tail of lanes
+                               that pick up a long trajectory last (e.g. sorted by a
+                               previous call's per-trajectory event counts).  Results do
+                               not depend on it.  Device memory for ml_simulate and
+                               ml_simulate_noalloc, host memory for ml_simulate_host;
+                               ignored by the plain form, the autotuner and the server.
+                               Entries outside [0, n_traj) are passed over; trajectories
+                               the order leaves out are not run (their outputs are not
+                               written)                                               */
 } ml_sim_params;
 
 /* Fills *p with the defaults above.  Returns ML_ERR_ARG if p is NULL. */

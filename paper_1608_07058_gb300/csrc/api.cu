@@ -497,6 +497,7 @@ void fill_args(const ml_model* m, const ml_sim_params& p, int64_t n_traj, const 
   a->newton_fp32 = p.precision == ML_PREC_FAST_FP32 && p.newton_precision == ML_NEWTON_FP32;
   a->stage_polls = p.stage_poll_limit;
   a->queue = nullptr;
+  a->order = p.form == ML_FORM_PERSISTENT ? p.queue_order : nullptr;
 }
 
 // Launches through a cached CUDA graph {queue reset, kernel}; kernel parameters are
@@ -605,7 +606,8 @@ int noalloc_prepare(const ml_model* m, int64_t n_traj, const double* theta, cons
     bool required;
   } ptrs[] = {{theta, "theta", false}, {x0, "x0", true},      {T, "T", true},
               {X, "X_out", true},      {r, "r_out", true},    {G, "G_out", true},
-              {status, "status_out", true}, {counters, "counters_out", false}};
+              {status, "status_out", true}, {counters, "counters_out", false},
+              {p.queue_order, "queue_order", false}};
   if (n_traj > 0) {
     for (const auto& q : ptrs) {
       if (!q.ptr) {
@@ -830,7 +832,8 @@ int ml_simulate_grid(const ml_model* cm, int64_t n_traj, const double* theta,
     bool required;
   } ptrs[] = {{theta, "theta", false}, {x0, "x0", true},      {T, "T", true},
               {X, "X_out", true},      {r, "r_out", true},    {G, "G_out", true},
-              {status, "status_out", true}, {counters, "counters_out", false}};
+              {status, "status_out", true}, {counters, "counters_out", false},
+              {p.form == ML_FORM_PERSISTENT ? p.queue_order : nullptr, "queue_order", false}};
   for (const auto& q : ptrs) {
     if (!q.ptr) {
       if (q.required) return fail(ML_ERR_ARG, "%s is NULL", q.name);
@@ -875,7 +878,12 @@ int ml_simulate_host(ml_model* m, int64_t n_traj, const double* theta, const int
   const size_t b_T = up16((T_per_traj ? n : 1) * 8);
   const size_t b_X = up16(n * N * 8), b_r = up16(n * M * 8), b_G = up16(n * M * 8);
   const size_t b_st = up16(n * 4), b_c = counters ? up16(n * 32) : 0;
-  const size_t total = b_theta + b_x0 + b_T + b_X + b_r + b_G + b_st + b_c;
+  ml_sim_params pq;
+  if (pp) pq = *pp;
+  else ml_default_params(&pq);
+  const bool ordered = pq.queue_order && pq.form == ML_FORM_PERSISTENT;
+  const size_t b_ord = ordered ? up16(n * 8) : 0;
+  const size_t total = b_theta + b_x0 + b_T + b_X + b_r + b_G + b_st + b_c + b_ord;
   DeviceState* st = nullptr;
   char* base = nullptr;
   {
@@ -921,10 +929,16 @@ int ml_simulate_host(ml_model* m, int64_t n_traj, const double* theta, const int
   uint32_t* d_st = reinterpret_cast<uint32_t*>(p);
   p += b_st;
   int64_t* d_c = counters ? reinterpret_cast<int64_t*>(p) : nullptr;
+  p += b_c;
+  if (ordered) {
+    int64_t* d_ord = reinterpret_cast<int64_t*>(p);
+    ML_CUDA_TRY(cudaMemcpyAsync(d_ord, pq.queue_order, n * 8, cudaMemcpyHostToDevice, stream));
+    pq.queue_order = d_ord;
+  }
   if (theta) ML_CUDA_TRY(cudaMemcpyAsync(d_theta, theta, n * M * 8, cudaMemcpyHostToDevice, stream));
   ML_CUDA_TRY(cudaMemcpyAsync(d_x0, x0, (x0_per_traj ? n : 1) * N * 8, cudaMemcpyHostToDevice, stream));
   ML_CUDA_TRY(cudaMemcpyAsync(d_T, T, (T_per_traj ? n : 1) * 8, cudaMemcpyHostToDevice, stream));
-  rc = ml_simulate(m, n_traj, d_theta, d_x0, x0_per_traj, d_T, T_per_traj, pp, seed, id_base,
+  rc = ml_simulate(m, n_traj, d_theta, d_x0, x0_per_traj, d_T, T_per_traj, &pq, seed, id_base,
                    d_X, d_r, d_G, d_st, d_c, stream);
   if (rc != ML_OK) return rc;
   ML_CUDA_TRY(cudaMemcpyAsync(X, d_X, n * N * 8, cudaMemcpyDeviceToHost, stream));
@@ -999,6 +1013,7 @@ int ml_autotune(ml_model* m, int64_t n_traj, const double* theta, const int64_t*
         c.block_size = b;
         c.ctas_per_sm = per_sm;
         c.use_graph = 0;
+        c.queue_order = nullptr;  // the sample is a prefix; an order for the full batch
         cands.push_back(c);
       }
     }
@@ -1058,6 +1073,7 @@ int ml_autotune(ml_model* m, int64_t n_traj, const double* theta, const int64_t*
   if (best) {
     *best = best_p;
     best->use_graph = p.use_graph;
+    best->queue_order = p.queue_order;
   }
   return ML_OK;
 }

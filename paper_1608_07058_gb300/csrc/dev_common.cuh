@@ -146,6 +146,24 @@ __device__ __forceinline__ double log_factorial_ref(long long k) {
 }  // namespace refmath
 
 // ---------------------------------------------------------------------------------
+// Persistent form: the next trajectory to run.  The k-th claim on the work queue is
+// trajectory order[k] when the caller gave an order (meant to be a permutation of
+// 0..n-1, longest first), else trajectory k.  Entries outside [0, n) are passed over, so a
+// malformed order cannot index out of bounds (trajectories it leaves out are not run).
+// Returns n_traj when the queue is exhausted.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ long long queue_claim(unsigned long long* queue, const int64_t* order,
+                                                 long long n_traj) {
+  for (;;) {
+    const long long k = (long long)atomicAdd(queue, 1ULL);
+    if (k >= n_traj) return n_traj;
+    if (!order) return k;
+    const long long i = __ldg(order + k);
+    if (i >= 0 && i < n_traj) return i;
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // Model staging: one bulk asynchronous copy (TMA engine, cp.async.bulk) of the model
 // tables from global to shared memory, completed on an mbarrier.  The wait is bounded
 // (poll_limit polls per thread); if it runs out the CTA waits again, bounded, for its copy

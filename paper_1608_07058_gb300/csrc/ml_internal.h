@@ -116,8 +116,10 @@ struct SimArgs {
   int32_t jacobian;  // ML_JAC_*
   int32_t newton_fp32;  // fast precision: FP32 implicit solve (ML_NEWTON_FP32)
   int32_t stage_polls;  // bounded wait for the model-table bulk copy
-  // persistent form: next unclaimed trajectory (zeroed before each launch)
+  // persistent form: next unclaimed trajectory (zeroed before each launch), and the
+  // optional order in which the queue hands trajectories out ([n_traj] or null)
   unsigned long long* queue;
+  const int64_t* order;
   // time-grid output: K_obs observation times (nondecreasing, >= 0, finite; checked on the
   // device, BAD_INPUT otherwise) and X_obs [n_traj][K_obs][N]; K_obs = 0 records nothing
   const double* t_obs;

@@ -286,6 +286,7 @@ int ml_server_create(size_t hbm_budget_bytes, int32_t max_inflight, const ml_sim
   if (p) s->params = *p;
   else ml_default_params(&s->params);
   s->params.use_graph = 0;  // concurrent launches: no shared graph executable
+  s->params.queue_order = nullptr;  // requests differ in size: no shared order
   if (cudaGetDevice(&s->device) != cudaSuccess) {
     cudaGetLastError();
     delete s;

@@ -1340,7 +1340,8 @@ constexpr int kSsaPerRound = 8;
 
 // Kernel: stage the model tables once per CTA, then run the lane state machine.  Plain
 // form (queue null): thread i runs trajectory i.  Persistent form: lanes claim trajectory
-// indices from the device queue and refill as soon as their trajectory ends.
+// indices from the device queue (in the caller's order, if any) and refill as soon as
+// their trajectory ends.
 template <int NM, int MM, class P>
 __global__ void ML_THREAD_BOUNDS k_thread(const ThreadModel<NM, MM>* __restrict__ gmd,
                                           const SimArgs args) {
@@ -1351,14 +1352,14 @@ __global__ void ML_THREAD_BOUNDS k_thread(const ThreadModel<NM, MM>* __restrict_
   using Lane = ThreadLane<NM, MM, P>;
   Lane L;
   L.mode = Lane::kIdle;
-  const long long first = args.queue ? (long long)atomicAdd(args.queue, 1ULL)
+  const long long first = args.queue ? queue_claim(args.queue, args.order, args.n_traj)
                                      : (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (first < args.n_traj) L.start(smd, args, first);
   for (;;) {
     if (L.mode == Lane::kDone) {
       L.finish(args, staged);
       if (args.queue) {
-        const long long nxt = (long long)atomicAdd(args.queue, 1ULL);
+        const long long nxt = queue_claim(args.queue, args.order, args.n_traj);
         if (nxt < args.n_traj) L.start(smd, args, nxt);
       }
     }
@@ -1385,7 +1386,7 @@ __global__ void ML_THREAD_BOUNDS k_thread_seq(const ThreadModel<NM, MM>* __restr
                                        args.stage_polls);
   using Lane = ThreadLane<NM, MM, P, kGrid>;
   Lane L;
-  long long i = args.queue ? (long long)atomicAdd(args.queue, 1ULL)
+  long long i = args.queue ? queue_claim(args.queue, args.order, args.n_traj)
                            : (long long)blockIdx.x * blockDim.x + threadIdx.x;
   while (i < args.n_traj) {
     L.start(smd, args, i);
@@ -1395,7 +1396,7 @@ __global__ void ML_THREAD_BOUNDS k_thread_seq(const ThreadModel<NM, MM>* __restr
     }
     L.finish(args, staged);
     if (!args.queue) break;
-    i = (long long)atomicAdd(args.queue, 1ULL);
+    i = queue_claim(args.queue, args.order, args.n_traj);
   }
 }
 

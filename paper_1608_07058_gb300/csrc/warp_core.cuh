@@ -944,7 +944,7 @@ __global__ void __launch_bounds__(256, ML_WARP_MIN_BLOCKS) k_warp(const WarpMode
   long long i;
   if (args.queue) {
     long long c = 0;
-    if (lane == 0) c = (long long)atomicAdd(args.queue, 1ULL);
+    if (lane == 0) c = queue_claim(args.queue, args.order, args.n_traj);
     i = __shfl_sync(0xffffffffu, c, 0);
   } else {
     i = (long long)blockIdx.x * warps + warp;
@@ -954,7 +954,7 @@ __global__ void __launch_bounds__(256, ML_WARP_MIN_BLOCKS) k_warp(const WarpMode
     if (!staged && lane == 0) args.status[i] |= ML_ST_STAGE_TIMEOUT;
     if (!args.queue) break;
     long long c = 0;
-    if (lane == 0) c = (long long)atomicAdd(args.queue, 1ULL);
+    if (lane == 0) c = queue_claim(args.queue, args.order, args.n_traj);
     i = __shfl_sync(0xffffffffu, c, 0);
   }
 }
