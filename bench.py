@@ -40,6 +40,26 @@ if ROOT not in sys.path:
 
 METRIC = "trajectories/s & leap-steps/s, batched vs plain launch, at oracle-matched stats"
 MAX_STEPS = 1_000_000
+_T0 = time.perf_counter()
+
+
+def stage(msg):
+    """Progress of the run on stderr (the JSON line is the only stdout output)."""
+    sys.stderr.write(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}\n")
+    sys.stderr.flush()
+
+
+def guarded(line, key, fn):
+    """Runs one optional leg; its failure is recorded in the line instead of losing the
+    headline measurement."""
+    stage(f"{key} ...")
+    try:
+        v = fn()
+        if v is not None:
+            line[key] = v
+    except Exception as e:  # noqa: BLE001 - recorded, the headline still prints
+        line[key] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        stage(f"{key} failed: {e}")
 
 
 def parse():
@@ -278,7 +298,8 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------
 # serving mix: continuous batching against one request per launch
 # ---------------------------------------------------------------------------------
-def run_serving(ml, seconds, rate_hz=200.0, seed=11, max_inflight=8, budget=8 << 30):
+def run_serving(ml, seconds, rate_hz=200.0, seed=11, max_inflight=8, budget=8 << 30,
+                n_drain=200):
     import threading
     import numpy as np
     from paper_1608_07058_gb300 import workloads as W
@@ -322,9 +343,12 @@ def run_serving(ml, seconds, rate_hz=200.0, seed=11, max_inflight=8, budget=8 <<
            "per_model": {W.config(m, n_traj=1).name: {**v, "traj_per_s": v["trajectories"] / max(v["busy_s"], 1e-9)}
                          for m, v in per_model.items()}}
 
-    # continuous batching: open-loop arrivals submitted by a thread at their times
+    # continuous batching: open-loop arrivals submitted by a thread at their times; the
+    # main thread takes the requests in arrival order, records each latency and frees the
+    # request's pinned buffers at once, so host memory holds only the requests in flight
     srv = ml.ml_server(budget, max_inflight, params)
     handles = [None] * len(reqs)
+    submitted = threading.Semaphore(0)
 
     def submitter(t_start):
         for i, q in enumerate(reqs):
@@ -334,32 +358,39 @@ def run_serving(ml, seconds, rate_hz=200.0, seed=11, max_inflight=8, budget=8 <<
             wl = q["workload"]
             handles[i] = srv.submit(models[q["model_index"]], wl.n_traj, wl.x0, wl.T, wl.theta,
                                     seed=wl.seed, traj_id_base=wl.traj_id_base)
+            submitted.release()
 
     t_start = time.perf_counter()
     th = threading.Thread(target=submitter, args=(t_start,))
     th.start()
-    th.join()
     lat = []
-    for h in handles:
+    for i in range(len(reqs)):
+        submitted.acquire()
+        h = handles[i]
         h.wait(-1)
-        lat.append(h.result()["latency_s"])
+        lat.append(h.latency()[0])
+        h.free()
+        handles[i] = None
+    th.join()
     t_end = time.perf_counter()
     st = srv.stats()
     # the completion of the last request, measured from the first arrival
     makespan = max(t_end - t_start - reqs[0]["arrival_s"], 1e-9)
-    for h in handles:
-        h.free()
-    # capacity: every request submitted at once, time to drain
+    # capacity: the first n_drain requests submitted at once, time to drain (bounded so
+    # that their pinned inputs and results fit in host memory)
+    drain_set = reqs[:n_drain]
+    drain_traj = sum(q["workload"].n_traj for q in drain_set)
     t0 = time.perf_counter()
     hs = [srv.submit(models[q["model_index"]], q["workload"].n_traj, q["workload"].x0,
                      q["workload"].T, q["workload"].theta, seed=q["workload"].seed,
-                     traj_id_base=q["workload"].traj_id_base) for q in reqs]
+                     traj_id_base=q["workload"].traj_id_base) for q in drain_set]
     for h in hs:
         h.wait(-1)
     drain = time.perf_counter() - t0
     for h in hs:
         h.free()
     srv.close()
+    drain_busy = float(sum(service[:n_drain]))
     lat = np.array(lat)
     span = reqs[-1]["arrival_s"] - reqs[0]["arrival_s"]
     return {"requests": len(reqs), "arrival_rate_hz": rate_hz, "window_s": seconds,
@@ -377,14 +408,18 @@ def run_serving(ml, seconds, rate_hz=200.0, seed=11, max_inflight=8, budget=8 <<
             "sustained_traj_per_s": total_traj / makespan,
             "sustained_vs_one_request_per_launch": (total_traj / makespan) / seq["sustained_traj_per_s"],
             "p99_latency_vs_one_request_per_launch": float(np.percentile(lat, 99)) * 1e3 / seq["p99_latency_ms"],
-            "saturated_traj_per_s": total_traj / drain,
-            "saturated_vs_one_request_per_launch": (total_traj / drain) / (total_traj / sum(service)),
+            "saturated_traj_per_s": drain_traj / drain,
+            "saturated_vs_one_request_per_launch": (drain_traj / drain) / (drain_traj / drain_busy),
+            "saturated_requests": len(drain_set),
             "peak_inflight": st["peak_inflight"], "max_inflight": max_inflight,
             "peak_device_bytes": st["peak_bytes"], "budget_bytes": budget,
             "one_request_per_launch": seq,
             "note": "sustained = all trajectories / (last completion - first arrival) at the "
                     "offered load; one request per launch is timed request by request and "
-                    "queued by the same arrival times"}
+                    "queued by the same arrival times; saturated = the first "
+                    f"{n_drain} requests submitted at once (and served one per launch)",
+            "inputs": "per-trajectory rate constants and horizons: B consecutive rows at a "
+                      "random offset of a per-model pool of 100,000 draws"}
 
 
 # ---------------------------------------------------------------------------------
@@ -502,7 +537,8 @@ def run_accuracy(ml, n=10_000, K=20, replicates=5, seed=500):
 
 
 SHAPE_NAMES = {1: "thread, round-based", 2: "warp", 3: "thread, round-based, occupancy build",
-               4: "thread, sequential per lane", 5: "thread, sequential per lane, occupancy build"}
+               4: "thread, sequential per lane", 5: "thread, sequential per lane, occupancy build",
+               6: "thread, phase pool", 7: "thread, phase pool, occupancy build"}
 
 
 def precision_label(ml, p):
@@ -669,7 +705,9 @@ def run_ours(args):
     B = w.n_traj
     # weak scaling: rank k simulates ids [k B, (k+1) B) of a world x B batch
     id_base, _ = ml.shard_bounds(world * B, rank, world)
+    stage(f"headline workload {workload_name(w)}: autotune ...")
     fast = tune(model, B, x0, T, theta, fast_params())
+    stage(f"headline: shape {int(fast.shape)}, block {int(fast.block_size)}; timing ...")
     clocks = ClockSampler(local)
     if not args.ncu:
         clocks.start()
@@ -715,8 +753,10 @@ def run_ours(args):
                         "run to its end, FP64 reference precision"}
 
     if not args.no_plain:
-        line["plain_fp64"] = plain_leg(model, B, x0, T, theta, w.crn, 5000, args.plain_budget_s)
-        line["batched_vs_plain"] = line["value"] / line["plain_fp64"]["value"]
+        guarded(line, "plain_fp64",
+                lambda: plain_leg(model, B, x0, T, theta, w.crn, 5000, args.plain_budget_s))
+        if "value" in line["plain_fp64"]:
+            line["batched_vs_plain"] = line["value"] / line["plain_fp64"]["value"]
 
     # roofline of the headline kernel: algorithmic operations against the issue rate
     ops_model = work_model(w.crn)
@@ -748,7 +788,7 @@ def run_ours(args):
         line["roofline"]["frac_at_measured_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 / 1e12)
 
     # end to end through the host-buffer entry point (pinned host memory)
-    if not args.ncu:
+    def e2e_leg():
         pin = lambda a: torch.as_tensor(a).pin_memory()
         hx0, hT = pin(w.x0), pin(w.T)
         hth = None if w.theta is None else pin(w.theta)
@@ -774,17 +814,24 @@ def run_ours(args):
         e2e_s = max_over_ranks((time.perf_counter() - t0) / k)
         h2d = hx0.numel() * 8 + hT.numel() * 8 + (0 if hth is None else hth.numel() * 8)
         d2h = sum(v.numel() * v.element_size() for v in hout.values())
-        line["e2e"] = {"value": world * B / e2e_s, "unit": "trajectories/s",
-                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                       "steps": k, "warmup": 1,
-                       "path": "ml_simulate_host: pinned host inputs (and the queue order) -> "
-                               "device -> simulate -> host"}
+        e2e = {"value": world * B / e2e_s, "unit": "trajectories/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": k, "warmup": 1,
+               "path": "ml_simulate_host: pinned host inputs (and the queue order) -> "
+                       "device -> simulate -> host"}
         if fast.queue_order:
-            line["e2e"]["h2d_bytes_per_step"] += B * 8
-            fast.queue_order = bench.order.data_ptr()
+            e2e["h2d_bytes_per_step"] += B * 8
+        return e2e
+
+    if not args.ncu:
+        dev_order = fast.queue_order
+        try:
+            guarded(line, "e2e", e2e_leg)
+        finally:
+            fast.queue_order = dev_order
 
     # CPU oracle baseline and oracle-matched statistics (rank 0, N = 1 only for the baseline)
-    if rank == 0 and not args.no_cpu and not args.ncu:
+    def cpu_leg():
         rate, n, dt, oout = oracle_rate(w, args.cpu_budget_s, seed=res_fast["last_seed"],
                                         first_id=id_base, jacobian=jac)
         if world == 1:
@@ -806,18 +853,18 @@ def run_ours(args):
                           "bad_status": res_fast["bad_status"]}
         line["parity"]["holm_pass_0.01"] = line["parity"]["fast_vs_oracle"]["holm_pass_0.01"]
 
+    if rank == 0 and not args.no_cpu and not args.ncu:
+        guarded(line, "cpu_baseline_and_parity", cpu_leg)  # sets its keys; an error stays here
+
     # the other workloads, each as a whole: fast (FP64 and FP32 Newton) and plain FP64
-    extras = {}
-    for cfg in [int(c) for c in args.extra_configs.split(",") if c.strip()]:
-        if cfg == args.config or args.ncu:
-            continue
+    def other_workload(cfg):
         we, me, x0e, Te, the = load(cfg)
         Be = we.n_traj
         entry = {"workload": workload_name(we)}
         for key, nw in (("fast_fp64_newton", ml.ML_NEWTON_FP64), ("fast_fp32_newton", ml.ML_NEWTON_FP32)):
             pe = tune(me, Be, x0e, Te, the, fast_params(nw))
             r = bench.timed(me, Be, x0e, Te, the, pe, 2000, id_base, args.steps,
-                                    args.warmup, budget_s=30.0)
+                            args.warmup, budget_s=30.0)
             mse = max_over_ranks(r["mean_ms"])
             ce = sum_over_ranks(r["counts"].astype(np.float64)) / r["steps"]
             opse = ops_from_counts(work_model(we.crn), ce / world)
@@ -831,22 +878,32 @@ def run_ours(args):
         if not args.no_plain:
             entry["plain_fp64"] = plain_leg(me, Be, x0e, Te, the, we.crn, 6000, 30.0)
             entry["batched_vs_plain"] = entry["fast_fp64_newton"]["value"] / entry["plain_fp64"]["value"]
-        extras[we.name] = entry
+        return entry
+
+    extras = {}
+    for cfg in [int(c) for c in args.extra_configs.split(",") if c.strip()]:
+        if cfg == args.config or args.ncu:
+            continue
+        guarded(extras, W.config(cfg, n_traj=1).name, lambda cfg=cfg: other_workload(cfg))
     if extras:
         line["other_workloads"] = extras
 
-    if rank == 0 and world == 1 and not args.ncu:
+    def pipe_peaks_leg():
         pk = ml.ml_measure_pipe_peaks()
-        line["pipe_peaks"] = {"fp64_fma_tflops": pk["fp64_fma_flops"] / 1e12,
-                              "fp32_fma_tflops": pk["fp32_fma_flops"] / 1e12,
-                              "mufu_lg2_tops": pk["mufu_lg2_ops"] / 1e12,
-                              "note": "project microbenchmarks (8 independent chains per thread, "
-                                      "8 CTAs of 256 threads per SM, ~20 ms each)"}
-        line["bayes_step"] = run_bayes(ml, res_fast["last_out"])
+        return {"fp64_fma_tflops": pk["fp64_fma_flops"] / 1e12,
+                "fp32_fma_tflops": pk["fp32_fma_flops"] / 1e12,
+                "mufu_lg2_tops": pk["mufu_lg2_ops"] / 1e12,
+                "note": "project microbenchmarks (8 independent chains per thread, "
+                        "8 CTAs of 256 threads per SM, ~20 ms each)"}
+
+    if rank == 0 and world == 1 and not args.ncu:
+        guarded(line, "pipe_peaks", pipe_peaks_leg)
+        guarded(line, "bayes_step", lambda: run_bayes(ml, res_fast["last_out"]))
         if not args.no_accuracy:
-            line["accuracy"] = run_accuracy(ml)
+            guarded(line, "accuracy", lambda: run_accuracy(ml))
     if rank == 0 and world == 1 and args.serving_seconds > 0 and not args.ncu:
-        line["serving"] = run_serving(ml, args.serving_seconds)
+        guarded(line, "serving", lambda: run_serving(ml, args.serving_seconds))
+    stage("done")
     if rank == 0:
         print(json.dumps(line, default=float), flush=True)
     if world > 1:

@@ -300,31 +300,44 @@ def serving_requests(n_requests: int, seed: int = 0, rate_hz: float = 200.0,
                      min_traj: int = 1_000, max_traj: int = 100_000, models=(0, 1, 2, 3),
                      horizon_scale=None, theta_shape=None):
     """Poisson-arrival request stream for the serving mix: each request picks a model
-    uniformly from `models`, a log-uniform trajectory count in [min_traj, max_traj], its
+    uniformly from `models`, a log-uniform trajectory count B in [min_traj, max_traj], its
     own per-trajectory rate constants theta ~ Gamma(shape, rate shape / k) around the
     model's rates k (shape from theta_shape, default SERVING_THETA_SHAPE) and its own
-    horizon: the model's horizon x horizon_scale[model] x U[0.5, 1] (default
-    SERVING_HORIZON_SCALE).  Returns a list of dicts with arrival time (s), Workload and a
-    distinct trajectory-id base."""
+    per-trajectory horizons: the model's horizon x horizon_scale[model] x U[0.5, 1]
+    (default SERVING_HORIZON_SCALE).
+
+    The rate constants and horizons are drawn once per model into a pool of max_traj
+    rows; a request takes B consecutive rows at a random offset (a view, no copy), so a
+    stream of thousands of requests holds a few pools in host memory instead of one batch
+    per request (the 50 x 100 network's rate constants alone are 800 bytes per
+    trajectory).  Requests differ in offset, size, horizon rows and trajectory ids, so
+    their random numbers never coincide.  Returns a list of dicts with arrival time (s),
+    Workload and a distinct trajectory-id base."""
     scales = dict(SERVING_HORIZON_SCALE if horizon_scale is None else horizon_scale)
     shapes = dict(SERVING_THETA_SHAPE if theta_shape is None else theta_shape)
     rng = np.random.default_rng(seed)
+    bases = {m: config(m, n_traj=1) for m in models}
+    pools = {}
+    for m in models:
+        crn = bases[m].crn
+        k = shapes.get(m, 2.0)
+        Tm = float(bases[m].T[0] if bases[m].T.shape[0] == 1 else 125.0) * scales.get(m, 1.0)
+        pools[m] = (np.ascontiguousarray(rng.gamma(k, crn.rates / k,
+                                                   size=(max_traj, crn.n_reactions))),
+                    np.ascontiguousarray(Tm * rng.uniform(0.5, 1.0, size=max_traj)))
     t = 0.0
     base = 0
     out = []
-    bases = {m: config(m, n_traj=1) for m in models}
     for q in range(n_requests):
         t += rng.exponential(1.0 / rate_hz)
         m = int(models[rng.integers(len(models))])
         B = int(np.floor(np.exp(rng.uniform(np.log(min_traj), np.log(max_traj)))))
+        B = min(max(B, 1), max_traj)
+        off = int(rng.integers(0, max_traj - B + 1))
         w0 = bases[m]
-        crn = w0.crn
-        k = shapes.get(m, 2.0)
-        theta = np.ascontiguousarray(rng.gamma(k, crn.rates / k, size=(B, crn.n_reactions)))
-        Tm = float(w0.T[0] if w0.T.shape[0] == 1 else 125.0) * scales.get(m, 1.0)
-        T = np.ascontiguousarray(Tm * rng.uniform(0.5, 1.0, size=B))
-        wl = Workload(f"req{q}_{w0.name}", crn, B, w0.x0.copy(), T, theta,
-                      seed=seed + 17, traj_id_base=base)
+        th_pool, T_pool = pools[m]
+        wl = Workload(f"req{q}_{w0.name}", w0.crn, B, w0.x0.copy(), T_pool[off:off + B],
+                      th_pool[off:off + B], seed=seed + 17, traj_id_base=base)
         base += B
         out.append({"arrival_s": t, "workload": wl, "model_index": m})
     return out
