@@ -25,6 +25,7 @@ ML_PREC_REF_FP64, ML_PREC_FAST_FP32 = 0, 1
 ML_FORM_PLAIN, ML_FORM_PERSISTENT = 0, 1
 ML_SHAPE_AUTO, ML_SHAPE_THREAD, ML_SHAPE_WARP, ML_SHAPE_THREAD_OCC, ML_SHAPE_THREAD_SEQ = 0, 1, 2, 3, 4
 ML_SHAPE_THREAD_SEQ_OCC = 5
+ML_SHAPE_THREAD_POOL, ML_SHAPE_THREAD_POOL_OCC = 6, 7
 ML_JAC_FD, ML_JAC_ANALYTIC = 0, 1
 ML_NEWTON_FP64, ML_NEWTON_FP32 = 0, 1
 
@@ -405,6 +406,13 @@ class ml_request:
                                        C.byref(lat), C.byref(q)))
         out["latency_s"], out["queue_s"] = lat.value, q.value
         return out
+
+    def latency(self) -> tuple:
+        """(latency_s, queue_s) of a finished request, without copying its results."""
+        lat, q = C.c_double(), C.c_double()
+        _check(lib().ml_request_result(C.c_void_p(self.handle), None, None, None, None, None,
+                                       C.byref(lat), C.byref(q)))
+        return lat.value, q.value
 
     def free(self):
         if self.handle:
