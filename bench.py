@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--no-order", action="store_true",
                     help="hand trajectories out in index order (no longest-first queue order)")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--generic", action="store_true",
+                    help="batched form on the precompiled kernels (no model-specialized kernels)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default launch shape (for very long workloads)")
     ap.add_argument("--shape", type=int, default=0,
@@ -670,7 +672,8 @@ def run_ours(args):
     def fast_params(newton_precision=newton):
         return ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32, form=ml.ML_FORM_PERSISTENT,
                                     use_graph=1, max_steps=MAX_STEPS, jacobian=jac,
-                                    newton_precision=newton_precision)
+                                    newton_precision=newton_precision,
+                                    specialize=0 if args.generic else 1)
 
     def plain_params(crn):
         return ml.ml_default_params(precision=ml.ML_PREC_REF_FP64, form=ml.ML_FORM_PLAIN,
@@ -698,7 +701,9 @@ def run_ours(args):
 
     def shape_of(p):
         return {"shape": SHAPE_NAMES.get(p.shape, "auto"), "shape_id": int(p.shape),
-                "block_size": int(p.block_size), "ctas_per_sm": int(p.ctas_per_sm)}
+                "block_size": int(p.block_size), "ctas_per_sm": int(p.ctas_per_sm),
+                "kernels": "compiled at run time for this model (tables as constants)"
+                if p.specialize else "precompiled (tables read at run time)"}
 
     # ---------------- the headline workload
     w, model, x0, T, theta = load(args.config, args.n_traj, args.horizon)

@@ -35,8 +35,10 @@
 #ifndef MATLEAP_H
 #define MATLEAP_H
 
+#ifndef __CUDACC_RTC__  /* the library's runtime-compiled kernels bring their own types */
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -94,6 +96,13 @@ extern "C" {
                                  of SSA bursts round by round                         */
 #define ML_SHAPE_THREAD_SEQ_OCC 5 /* fast precision only: the sequential per-lane driver
                                      in the occupancy build                           */
+#define ML_SHAPE_THREAD_POOL 6 /* persistent form only: one trajectory per thread at a
+                                  time, each warp keeping 64 trajectories in shared
+                                  memory and running one phase (SSA slices or leap
+                                  evaluations) for 32 of them per round, so that its
+                                  lanes do not diverge between the phases             */
+#define ML_SHAPE_THREAD_POOL_OCC 7 /* fast precision, persistent form: the pool driver
+                                      in the occupancy build                          */
 
 /* ---- Jacobian of the implicit solve (Section 1: estimated numerically, or the
  *      symbolic Jacobian of Section 3).  Every FP64 solve follows the choice; the FP32
@@ -117,7 +126,8 @@ typedef struct ml_model ml_model;
  * pe_delta 0.05, stiff_ratio 100, newton_tol 1e-10, newton_maxit 20, fd_h 1e-7,
  * max_steps 1e8, max_reject 64, mode ADAPTIVE, precision REF_FP64, form PLAIN,
  * shape AUTO, block_size 0 (tuned or default), ctas_per_sm 0, use_graph 0,
- * jacobian FD, newton_precision FP64, stage_poll_limit 4194304, queue_order NULL. */
+ * jacobian FD, newton_precision FP64, stage_poll_limit 4194304, queue_order NULL,
+ * specialize 0. */
 typedef struct {
   double eps;             /* Cao 2006 bound on the relative change of each reactant    */
   int32_t n_c;            /* critical threshold (Section 2)                            */
@@ -155,6 +165,14 @@ typedef struct {
                                Entries outside [0, n_traj) are passed over; trajectories
                                the order leaves out are not run (their outputs are not
                                written)                                               */
+  int32_t specialize;     /* thread-per-trajectory shapes: 1 = run kernels compiled for
+                               this model, its tables built in as constants (the first
+                               call per model, precision and driver compiles one, about
+                               a second, and loads it on the device), 0 = the
+                               precompiled kernels that read the tables at run time.
+                               Results are identical (reference precision: bitwise).
+                               Ignored by the warp shape, time-grid calls, the server
+                               and ml_simulate_noalloc.                                */
 } ml_sim_params;
 
 /* Fills *p with the defaults above.  Returns ML_ERR_ARG if p is NULL. */
@@ -212,13 +230,17 @@ int ml_simulate_host(ml_model* model, int64_t n_traj, const double* theta,
                      uint64_t traj_id_base, int64_t* X_out, int64_t* r_out, double* G_out,
                      uint32_t* status_out, int64_t* counters_out, void* cuda_stream);
 
-/* Project autotuner: times candidate kernel shapes (trajectory per thread or per warp,
- * threads per CTA, resident CTAs per SM up to what fits at once) on the first
- * min(n_traj, n_sample) trajectories of the given inputs, with p's mode/precision/form
- * (one warm-up run, then the median of five timed runs per candidate; candidates in a
- * fixed order, a later one replacing the best so far only when more than 3 % faster),
- * and stores the choice in the model (used when a later call passes block_size = 0) and
- * in *best.  Synchronizes cuda_stream.  Uses internal scratch outputs. */
+/* Project autotuner: times candidate kernel shapes (trajectory per thread -- round-based,
+ * sequential or pool driver, each also in the occupancy build where that exists -- or per
+ * warp, threads per CTA 64/128/256, resident CTAs per SM 0 (as many as fit), 1, 2 or 4
+ * up to what fits at once; a model that fits one thread tries the warp kernel in one
+ * launch shape only) on the first min(n_traj, n_sample) trajectories of the given
+ * inputs, with p's mode/precision/form (one warm-up run, then the median of three timed
+ * runs per candidate; a candidate whose warm-up takes more than twice the best median so
+ * far is dropped; candidates in a fixed order, a later one replacing the best so far only
+ * when more than 3 % faster), and stores the choice in the model (used when a later call
+ * passes block_size = 0) and in *best.  Synchronizes cuda_stream.  Uses internal scratch
+ * outputs. */
 int ml_autotune(ml_model* model, int64_t n_traj, const double* theta, const int64_t* x0,
                 int32_t x0_per_traj, const double* T, int32_t T_per_traj,
                 const ml_sim_params* p, uint64_t seed, int64_t n_sample,

@@ -43,14 +43,15 @@ def _units():
     for fast in (0, 1):
         for v in range(N_THREAD_VARIANTS):
             u += _thread_units("fast" if fast else "ref", [f"-DML_FAST={fast}", f"-DML_VARIANT={v}"]
-                               + ([] if fast else ["-fmad=false"]), v, (0, 1, 2))
+                               + ([] if fast else ["-fmad=false"]), v, (0, 1, 2, 3))
         if fast:
             for v in range(N_THREAD_VARIANTS):
                 u += _thread_units("fastocc", ["-DML_FAST=1", f"-DML_VARIANT={v}",
-                                               "-DML_THREAD_MIN_BLOCKS=2"], v, (0, 1))
+                                               "-DML_THREAD_MIN_BLOCKS=2"], v, (0, 1, 3))
         u.append(("kern_warp.cu", f"kw_{'fast' if fast else 'ref'}.o",
                   [f"-DML_FAST={fast}"] + ([] if fast else ["-fmad=false"])))
     u.append(("api.cu", "api.o", []))
+    u.append(("jit.cu", "jit.o", []))
     u.append(("noalloc.cu", "noalloc.o", []))
     u.append(("server.cu", "server.o", []))
     u.append(("bayes.cu", "bayes.o", ["-fmad=false"]))
@@ -61,6 +62,38 @@ def _units():
 
 def _sources():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "matleap.h")]
+
+
+# Headers compiled again at run time for the model-specialized kernels (jit.cu): embedded
+# into the library as strings, so the library does not need its source tree at run time.
+JIT_HEADERS = [("thread_core.cuh", CSRC), ("dev_common.cuh", CSRC), ("ml_internal.h", CSRC),
+               ("matleap.h", INCLUDE)]
+
+
+def _write_jit_sources():
+    out = ["// Generated by build.py: kernel headers for runtime compilation.", "#pragma once",
+           f"constexpr int kJitHeaderCount = {len(JIT_HEADERS)};"]
+    names, texts = [], []
+    for name, d in JIT_HEADERS:
+        text = open(os.path.join(d, name)).read()
+        assert ")MLJIT\"" not in text
+        names.append(f'"{name}"')
+        texts.append('R"MLJIT(' + text + ')MLJIT"')
+    out.append("static const char* const kJitHeaderName[] = {" + ", ".join(names) + "};")
+    out.append("static const char* const kJitHeaderText[] = {\n" + ",\n".join(texts) + "};")
+    path = os.path.join(BUILD, "jit_sources.h")
+    text = "\n".join(out) + "\n"
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as f:
+            f.write(text)
+
+
+def _cuda_lib_dir(nvcc):
+    root = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    for d in (os.path.join(root, "lib64"), os.path.join(root, "lib")):
+        if os.path.exists(os.path.join(d, "libnvrtc.so")):
+            return d
+    raise RuntimeError(f"libnvrtc.so not found next to {nvcc}")
 
 
 def up_to_date():
@@ -75,8 +108,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    _write_jit_sources()
     common = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-              "-I", INCLUDE, "-I", CSRC]
+              "-I", INCLUDE, "-I", CSRC, "-I", BUILD]
     jobs = []
     for src, obj, flags in _units():
         cmd = common + flags + ["-c", os.path.join(CSRC, src), "-o", os.path.join(BUILD, obj)]
@@ -95,7 +129,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{res.stderr}")
     objs = [os.path.join(BUILD, o) for _, o, _ in _units()]
     tmp = LIB + ".tmp"
-    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    libdir = _cuda_lib_dir(nvcc)
+    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-L", libdir, "-lnvrtc",
+            "-Xlinker", "-rpath", "-Xlinker", libdir]
     res = subprocess.run(link, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(link)}\n{res.stderr}")

@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 
+#include "jit.h"
 #include "matleap.h"
 #include "ml_internal.h"
 
@@ -56,6 +57,13 @@ struct Tuned {
   int shape = 0, block = 0, ctas_per_sm = 0;
 };
 
+// A model-specialized kernel, loaded as a CUDA library (valid in every context).
+struct JitKernel {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kernel = nullptr;
+  int pool_words = 0;
+};
+
 struct DeviceState {
   void* thread_tables[mlk::kThreadVariants] = {};
   void* warp_tables = nullptr;
@@ -86,6 +94,7 @@ struct ml_model {
   int thread_variant = -1;                // smallest thread variant holding the model
   std::vector<uint8_t> host_thread_tables;  // its tables (for the allocation-free path)
   size_t warp_table_bytes = 0;
+  std::map<int, JitKernel> jit;  // specialized kernels by (precision, driver, occupancy build)
 };
 
 namespace {
@@ -103,6 +112,7 @@ std::vector<uint8_t> build_thread_tables(const ml_model& m) {
       const bool in = j < m.M && s < m.N;
       t.ord[j][s] = in ? (int8_t)m.ord[j * m.N + s] : 0;
       t.nu[j][s] = in ? (int8_t)m.nu[j * m.N + s] : 0;
+      t.nuf[j][s] = (float)t.nu[j][s];
     }
   }
   for (int j = 0; j < m.M && j < MM; ++j)  // the variant always holds the model (M <= MM)
@@ -231,6 +241,31 @@ mlk::KernelEntry thread_seq_entry(int precision, int variant, bool occ = false) 
   }
 }
 
+mlk::KernelEntry thread_pool_entry(int precision, int variant, bool occ = false) {
+  if (precision == ML_PREC_FAST_FP32 && occ) {
+    switch (variant) {
+      case 0: return mlk::thread_pool_entry_fastocc_0();
+      case 1: return mlk::thread_pool_entry_fastocc_1();
+      case 2: return mlk::thread_pool_entry_fastocc_2();
+      default: return mlk::thread_pool_entry_fastocc_3();
+    }
+  }
+  if (precision == ML_PREC_FAST_FP32) {
+    switch (variant) {
+      case 0: return mlk::thread_pool_entry_fast_0();
+      case 1: return mlk::thread_pool_entry_fast_1();
+      case 2: return mlk::thread_pool_entry_fast_2();
+      default: return mlk::thread_pool_entry_fast_3();
+    }
+  }
+  switch (variant) {
+    case 0: return mlk::thread_pool_entry_ref_0();
+    case 1: return mlk::thread_pool_entry_ref_1();
+    case 2: return mlk::thread_pool_entry_ref_2();
+    default: return mlk::thread_pool_entry_ref_3();
+  }
+}
+
 mlk::KernelEntry thread_entry(int precision, int variant, bool occ = false) {
   if (precision == ML_PREC_FAST_FP32 && occ) {
     switch (variant) {
@@ -304,11 +339,15 @@ int check_params(const ml_sim_params& p) {
     return fail(ML_ERR_ARG, "unknown precision %d", p.precision);
   if (p.form != ML_FORM_PLAIN && p.form != ML_FORM_PERSISTENT)
     return fail(ML_ERR_ARG, "unknown form %d", p.form);
-  if (p.shape < ML_SHAPE_AUTO || p.shape > ML_SHAPE_THREAD_SEQ_OCC)
+  if (p.shape < ML_SHAPE_AUTO || p.shape > ML_SHAPE_THREAD_POOL_OCC)
     return fail(ML_ERR_ARG, "unknown shape %d", p.shape);
-  if ((p.shape == ML_SHAPE_THREAD_OCC || p.shape == ML_SHAPE_THREAD_SEQ_OCC) &&
+  if ((p.shape == ML_SHAPE_THREAD_OCC || p.shape == ML_SHAPE_THREAD_SEQ_OCC ||
+       p.shape == ML_SHAPE_THREAD_POOL_OCC) &&
       p.precision != ML_PREC_FAST_FP32)
     return fail(ML_ERR_ARG, "the 128-register thread build exists in fast precision only");
+  if ((p.shape == ML_SHAPE_THREAD_POOL || p.shape == ML_SHAPE_THREAD_POOL_OCC) &&
+      p.form != ML_FORM_PERSISTENT)
+    return fail(ML_ERR_ARG, "the pool driver runs in the persistent form only");
   if (p.block_size != 0 && (p.block_size < 32 || p.block_size > 256 || p.block_size % 32))
     return fail(ML_ERR_ARG, "block_size must be 0 or a multiple of 32 in [32, 256]");
   if (p.ctas_per_sm < 0 || p.ctas_per_sm > 32)
@@ -318,6 +357,7 @@ int check_params(const ml_sim_params& p) {
   if (p.newton_precision != ML_NEWTON_FP64 && p.newton_precision != ML_NEWTON_FP32)
     return fail(ML_ERR_ARG, "unknown newton_precision %d", p.newton_precision);
   if (p.stage_poll_limit < 0) return fail(ML_ERR_ARG, "stage_poll_limit must be >= 0");
+  if (p.specialize != 0 && p.specialize != 1) return fail(ML_ERR_ARG, "specialize must be 0 or 1");
   return ML_OK;
 }
 
@@ -366,9 +406,55 @@ int ensure_tables(ml_model* m, DeviceState& st, int shape, int variant) {
   return ML_OK;
 }
 
+// The specialized kernel for (precision, driver, occupancy build), compiled and loaded at
+// first use (model lock held).
+int jit_entry(ml_model* m, int variant, int precision, int driver, bool occ,
+              mlk::KernelEntry* out) {
+  const int key = precision * 100 + driver * 10 + (occ ? 1 : 0);
+  auto it = m->jit.find(key);
+  if (it == m->jit.end()) {
+    mlk::JitSpec k;
+    k.NM = mlk::kThreadN[variant];
+    k.MM = mlk::kThreadM[variant];
+    k.N = m->N;
+    k.M = m->M;
+    k.ord = m->ord.data();
+    k.nu = m->nu.data();
+    k.rates = m->rates.data();
+    k.partner = m->partner.data();
+    k.isreact = m->isreact.data();
+    k.hor = m->hor.data();
+    k.n_pairs = m->n_pairs;
+    k.precision_ref = precision == ML_PREC_REF_FP64;
+    k.driver = driver;
+    k.occ = occ;
+    std::vector<char> cubin;
+    std::string log;
+    if (mlk::jit_compile(mlk::jit_source(k), k.precision_ref, &cubin, &log) != 0)
+      return fail(ML_ERR_CUDA, "runtime compilation of the specialized kernel failed: %.400s",
+                  log.c_str());
+    JitKernel jk;
+    ML_CUDA_TRY(cudaLibraryLoadData(&jk.lib, cubin.data(), nullptr, nullptr, 0, nullptr,
+                                    nullptr, 0));
+    cudaError_t e = cudaLibraryGetKernel(&jk.kernel, jk.lib, "ml_jit_kernel");
+    if (e != cudaSuccess) {
+      cudaLibraryUnload(jk.lib);
+      return cuda_fail(e, "specialized kernel lookup");
+    }
+    jk.pool_words = mlk::lane_record_words(k.NM, k.MM, k.precision_ref);
+    it = m->jit.emplace(key, jk).first;
+  }
+  out->launch = nullptr;  // launched through cudaLaunchKernel
+  out->kernel = reinterpret_cast<const void*>(it->second.kernel);
+  out->pool_words = driver == mlk::kJitPool ? it->second.pool_words : 0;
+  return ML_OK;
+}
+
 struct Plan {
+  bool jit = false;
   bool occ = false;
   bool seq = false;
+  bool pool = false;
   bool grid_out = false;  // kernel build with time-grid output
   int shape = ML_SHAPE_THREAD;
   int variant = 0;
@@ -394,29 +480,42 @@ int make_plan(ml_model* m, DeviceState& st, const ml_sim_params& p, int64_t n_tr
   // a call with time-grid output runs the grid build of the sequential driver (the
   // drivers give identical results), without the occupancy bound
   const bool occ = !grid_out &&
-                   (shape == ML_SHAPE_THREAD_OCC || shape == ML_SHAPE_THREAD_SEQ_OCC) &&
+                   (shape == ML_SHAPE_THREAD_OCC || shape == ML_SHAPE_THREAD_SEQ_OCC ||
+                    shape == ML_SHAPE_THREAD_POOL_OCC) &&
                    p.precision == ML_PREC_FAST_FP32;
   const bool seq = grid_out || shape == ML_SHAPE_THREAD_SEQ || shape == ML_SHAPE_THREAD_SEQ_OCC;
+  const bool pool = !grid_out && p.form == ML_FORM_PERSISTENT &&
+                    (shape == ML_SHAPE_THREAD_POOL || shape == ML_SHAPE_THREAD_POOL_OCC);
   if (shape != ML_SHAPE_WARP) shape = ML_SHAPE_THREAD;
   if (shape == ML_SHAPE_THREAD && variant < 0)
     return fail(ML_ERR_UNSUPPORTED, "model %dx%d is too large for one thread per trajectory",
                 m->N, m->M);
   if (shape == ML_SHAPE_WARP && !warp_fits(*m))
     return fail(ML_ERR_UNSUPPORTED, "model %dx%d is too large for the warp kernel", m->N, m->M);
-  const mlk::KernelEntry entry =
+  const bool jit = p.specialize && shape == ML_SHAPE_THREAD && !grid_out;
+  mlk::KernelEntry entry =
       grid_out ? (shape == ML_SHAPE_THREAD ? thread_seq_grid_entry(p.precision, variant)
                                            : warp_grid_entry(p.precision))
       : shape == ML_SHAPE_THREAD
           ? (seq ? thread_seq_entry(p.precision, variant, occ)
-                 : thread_entry(p.precision, variant, occ))
+                 : pool ? thread_pool_entry(p.precision, variant, occ)
+                        : thread_entry(p.precision, variant, occ))
           : warp_entry(p.precision);
-  if (!entry.kernel || !entry.launch)
+  if (jit) {
+    const int rc = jit_entry(m, variant, p.precision,
+                             seq ? mlk::kJitSequential : pool ? mlk::kJitPool : mlk::kJitRounds,
+                             occ, &entry);
+    if (rc != ML_OK) return rc;
+  } else if (!entry.kernel || !entry.launch) {
     return fail(ML_ERR_UNSUPPORTED, "no kernel built for this shape and precision");
+  }
   int rc = ensure_tables(m, st, shape, variant);
   if (rc != ML_OK) return rc;
   plan->shape = shape;
+  plan->jit = jit;
   plan->occ = occ;
   plan->seq = seq;
+  plan->pool = pool;
   plan->grid_out = grid_out;
   plan->variant = variant;
   plan->entry = entry;
@@ -426,11 +525,19 @@ int make_plan(ml_model* m, DeviceState& st, const ml_sim_params& p, int64_t n_tr
                            : (tuned_here && tuned->block ? tuned->block
                                                          : (shape == ML_SHAPE_THREAD ? 128 : 128));
   if (plan->occ && block > 128) block = 128;  // the occupancy build is bounded to 128 threads
-  const int per_cta = shape == ML_SHAPE_THREAD ? block : block / 32;  // trajectories
+  if (pool) {  // the warps' trajectory records must fit in one CTA's shared memory
+    const size_t per_warp = (size_t)entry.pool_words * mlk::kPoolSlots * 4;
+    const int max_warps = (int)((227 * 1024 - 1024) / per_warp);
+    if (max_warps < 1) return fail(ML_ERR_UNSUPPORTED, "pool records too large for shared memory");
+    if (block / 32 > max_warps) block = 32 * max_warps;
+  }
+  const int per_cta = shape == ML_SHAPE_THREAD ? (pool ? block / 32 * mlk::kPoolSlots : block)
+                                               : block / 32;  // trajectories
   plan->smem = shape == ML_SHAPE_WARP
                    ? mlk::warp_smem_bytes(block / 32, m->N, m->M, p.precision,
                                           p.newton_precision == ML_NEWTON_FP32)
-                   : 0;
+               : pool ? (size_t)(block / 32) * entry.pool_words * mlk::kPoolSlots * 4
+                      : 0;
   if (plan->smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(plan->entry.kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -504,8 +611,10 @@ void fill_args(const ml_model* m, const ml_sim_params& p, int64_t n_traj, const 
 // updated in place when they change.
 int launch_graph(DeviceState& st, const ml_sim_params& p, const Plan& plan,
                  mlk::SimArgs& a, cudaStream_t stream) {
-  const int key2 = (plan.shape == ML_SHAPE_THREAD ? plan.variant + (plan.occ ? 50 : 0) + (plan.seq ? 25 : 0) : 100) +
-                   (plan.grid_out ? 1000 : 0);
+  const int key2 = (plan.shape == ML_SHAPE_THREAD ? plan.variant + (plan.occ ? 50 : 0) +
+                                                      (plan.seq ? 25 : 0) + (plan.pool ? 12 : 0)
+                                                    : 100) +
+                   (plan.grid_out ? 1000 : 0) + (plan.jit ? 500 : 0);
   GraphCache& gc = st.graphs[{p.precision, key2}];
   const void* tables = plan.tables;
   void* kargs[2] = {const_cast<void**>(&tables), &a};
@@ -547,7 +656,15 @@ int run_plan(ml_model* m, DeviceState& st, const ml_sim_params& p, const Plan& p
     }
     ML_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), stream));
   }
-  cudaError_t e = plan.entry.launch(plan.tables, a, plan.grid, plan.block, plan.smem, stream);
+  cudaError_t e;
+  if (plan.entry.launch) {
+    e = plan.entry.launch(plan.tables, a, plan.grid, plan.block, plan.smem, stream);
+  } else {  // a specialized kernel: same parameters (tables, SimArgs)
+    const void* tables = plan.tables;
+    void* kargs[2] = {const_cast<void**>(&tables), &a};
+    e = cudaLaunchKernel(plan.entry.kernel, dim3((unsigned)plan.grid), dim3((unsigned)plan.block),
+                         kargs, plan.smem, stream);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   m->last_launches = 1;
   return ML_OK;
@@ -771,6 +888,8 @@ int ml_model_destroy(ml_model* m) {
     if (st.ws) cudaFree(st.ws);
   }
   cudaSetDevice(cur);
+  for (auto& kv : m->jit)
+    if (kv.second.lib) cudaLibraryUnload(kv.second.lib);
   delete m;
   return ML_OK;
 }
@@ -980,15 +1099,20 @@ int ml_autotune(ml_model* m, int64_t n_traj, const double* theta, const int64_t*
   const int thread_ok = thread_variant_for(*m) >= 0;
   const int warp_ok = warp_fits(*m);
   std::vector<ml_sim_params> cands;
-  for (int shape = ML_SHAPE_THREAD; shape <= ML_SHAPE_THREAD_SEQ_OCC; ++shape) {
+  for (int shape = ML_SHAPE_THREAD; shape <= ML_SHAPE_THREAD_POOL_OCC; ++shape) {
     const bool thread_like = shape != ML_SHAPE_WARP;
-    const bool occ_shape = shape == ML_SHAPE_THREAD_OCC || shape == ML_SHAPE_THREAD_SEQ_OCC;
+    const bool occ_shape = shape == ML_SHAPE_THREAD_OCC || shape == ML_SHAPE_THREAD_SEQ_OCC ||
+                           shape == ML_SHAPE_THREAD_POOL_OCC;
+    const bool pool_shape = shape == ML_SHAPE_THREAD_POOL || shape == ML_SHAPE_THREAD_POOL_OCC;
     if ((thread_like && !thread_ok) || (shape == ML_SHAPE_WARP && !warp_ok)) continue;
     if (occ_shape && p.precision != ML_PREC_FAST_FP32) continue;
+    if (pool_shape && p.form != ML_FORM_PERSISTENT) continue;
     if (p.shape != ML_SHAPE_AUTO && p.shape != shape) continue;
     const int blocks[] = {64, 128, 256};
     for (int b : blocks) {
       if (occ_shape && b > 128) continue;
+      // a model that fits one thread tries the warp kernel in one launch shape only
+      if (shape == ML_SHAPE_WARP && thread_ok && b != 128) continue;
       // CTAs per SM beyond what can be resident at once only queue behind the others
       int resident = 0;
       {
@@ -1004,9 +1128,10 @@ int ml_autotune(ml_model* m, int64_t n_traj, const double* theta, const int64_t*
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, plan.entry.kernel, b,
                                                         plan.smem);
       }
-      const int per_sm_opts[] = {0, 1, 2, 4, 8};
+      const int per_sm_opts[] = {0, 1, 2, 4};
       for (int per_sm : per_sm_opts) {
         if (p.form != ML_FORM_PERSISTENT && per_sm != 0) continue;
+        if (shape == ML_SHAPE_WARP && thread_ok && per_sm != 0) continue;
         if (per_sm > 0 && resident > 0 && per_sm >= resident) continue;  // 0 covers it
         ml_sim_params c = p;
         c.shape = shape;
@@ -1021,19 +1146,20 @@ int ml_autotune(ml_model* m, int64_t n_traj, const double* theta, const int64_t*
   // Candidates run in a fixed order; each is timed kTimed times after one warm-up and
   // scored by the median.  A later candidate replaces the incumbent only if it is more
   // than 3 % faster, so run-to-run noise does not flip the choice between near-equal
-  // shapes.
-  constexpr int kTimed = 5;
+  // shapes.  A candidate whose warm-up run takes more than twice the incumbent's median
+  // is not timed further.
+  constexpr int kTimed = 3;
   float best_ms = 1e30f;
   ml_sim_params best_p = p;
   for (const ml_sim_params& c : cands) {
     float t_rep[kTimed];
     bool ok = true;
     for (int rep = 0; rep <= kTimed && ok; ++rep) {
-      if (rep > 0) cudaEventRecord(e0, stream);
+      cudaEventRecord(e0, stream);
       int r2 = ml_simulate(m, n, theta, x0, x0_per_traj, T, T_per_traj, &c, seed, 0, X, r, G,
                            stt, cnt, stream);
       if (r2 != ML_OK) ok = false;
-      if (rep > 0 && ok) {
+      if (ok) {
         cudaEventRecord(e1, stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) {
           cudaEventDestroy(e0);
@@ -1043,7 +1169,8 @@ int ml_autotune(ml_model* m, int64_t n_traj, const double* theta, const int64_t*
         }
         float t = 0.f;
         cudaEventElapsedTime(&t, e0, e1);
-        t_rep[rep - 1] = t;
+        if (rep == 0 && t > 2.f * best_ms) ok = false;  // clearly slower: not timed further
+        if (rep > 0) t_rep[rep - 1] = t;
       }
     }
     if (!ok) continue;

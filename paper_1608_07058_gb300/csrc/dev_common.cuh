@@ -1,9 +1,11 @@
 // Device building blocks: counter-based random numbers, the FP64 elementary functions
 // of the reference-precision path, and bulk staging of model tables into shared memory.
 #pragma once
+#ifndef __CUDACC_RTC__  // runtime compilation (model-specialized kernels) brings its own types
 #include <cstdint>
 
 #include <cuda_runtime.h>
+#endif
 
 namespace mlk {
 

@@ -5,9 +5,9 @@
 //   CTA, about 168 registers, more resident warps, some spilling), offered to the
 //   autotuner as a separate shape.  The plain builds also carry the sequential driver
 //   with time-grid output.
-//   ML_PART (optional): build only the round-based driver (0), the sequential driver (1)
-//   or its time-grid build (2) of this variant, so that the large generic variant's
-//   kernels compile in parallel units; unset, the unit holds all of them.
+//   ML_PART (optional): build only the round-based driver (0), the sequential driver (1),
+//   its time-grid build (2) or the pool driver (3) of this variant, so that the large
+//   generic variant's kernels compile in parallel units; unset, the unit holds all of them.
 #include "thread_core.cuh"
 
 #ifndef ML_PART
@@ -52,6 +52,14 @@ cudaError_t launch_seq(const void* dm, const SimArgs& a, int grid, int block, si
   return cudaGetLastError();
 }
 #endif
+#if ML_HAS_PART(3)
+cudaError_t launch_pool(const void* dm, const SimArgs& a, int grid, int block, size_t smem,
+                        cudaStream_t s) {
+  k_thread_pool<kNM, kMM, Prec><<<grid, block, smem, s>>>(
+      static_cast<const ThreadModel<kNM, kMM>*>(dm), a);
+  return cudaGetLastError();
+}
+#endif
 #if !(ML_FAST && ML_THREAD_MIN_BLOCKS == 2) && ML_HAS_PART(2)
 cudaError_t launch_seq_grid(const void* dm, const SimArgs& a, int grid, int block, size_t smem,
                             cudaStream_t s) {
@@ -71,6 +79,12 @@ KernelEntry ML_CAT(thread_seq_grid_entry_, ML_PNAME, ML_VARIANT)() {
 #if ML_HAS_PART(0)
 KernelEntry ML_CAT(thread_entry_, ML_PNAME, ML_VARIANT)() {
   return KernelEntry{&launch, reinterpret_cast<const void*>(&k_thread<kNM, kMM, Prec>)};
+}
+#endif
+#if ML_HAS_PART(3)
+KernelEntry ML_CAT(thread_pool_entry_, ML_PNAME, ML_VARIANT)() {
+  return KernelEntry{&launch_pool, reinterpret_cast<const void*>(&k_thread_pool<kNM, kMM, Prec>),
+                     ThreadLane<kNM, kMM, Prec>::kWords};
 }
 #endif
 #if ML_HAS_PART(1)

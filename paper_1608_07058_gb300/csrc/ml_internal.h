@@ -1,10 +1,12 @@
 // Internal declarations shared by the CUDA library's translation units (host API and
 // kernels).  Nothing here is visible through include/matleap.h.
 #pragma once
+#ifndef __CUDACC_RTC__  // runtime compilation (model-specialized kernels) brings its own types
 #include <cstddef>
 #include <cstdint>
 
 #include <cuda_runtime.h>
+#endif
 
 namespace mlk {
 
@@ -21,6 +23,14 @@ constexpr int kThreadM[kThreadVariants] = {2, 4, 6, 16};
 constexpr long long kCountLimit = 1LL << 62;
 constexpr long long kLeapLimitInt = 1LL << 48;
 constexpr double kLeapLimit = 281474976710656.0;  // 2^48
+
+// Trajectories each warp of the pool driver keeps in shared memory, and the 32-bit words
+// of one trajectory's record there (mode, id, status, step, reject run, burst index and
+// length; trajectory index, t, T; theta; x, r, G and the four event counters).
+constexpr int kPoolSlots = 64;
+__host__ __device__ constexpr int lane_record_words(int NM, int MM, bool ref) {
+  return 13 + (ref ? 2 : 1) * MM + 2 * NM + 4 * MM + 8;
+}
 
 // Warp-per-trajectory capacities.
 constexpr int kWarpMaxN = 64;
@@ -41,7 +51,9 @@ enum : uint8_t {
 // Staged into shared memory at kernel start by one bulk copy.
 template <int NM, int MM>
 struct alignas(16) ThreadModel {
+  static constexpr bool kCompiled = false;  // tables read at run time (see JitModel)
   double rates[MM];
+  float nuf[MM][NM];    // nu_js as FP32 (updates of the fast SSA slice's FP32 state copy)
   int8_t ord[MM][NM];   // m_js
   int8_t nu[MM][NM];    // nu_js
   int8_t partner[MM];   // for the lower reaction of a reversible pair: the other; else -1
@@ -127,6 +139,7 @@ struct SimArgs {
   int32_t K_obs;
 };
 
+#ifndef __CUDACC_RTC__
 // One compiled kernel variant: its launcher and its function pointer (for occupancy
 // queries and CUDA-graph kernel nodes).  Every kernel takes (model tables, SimArgs).
 using LaunchFn = cudaError_t (*)(const void* dmodel, const SimArgs& a, int grid, int block,
@@ -134,6 +147,7 @@ using LaunchFn = cudaError_t (*)(const void* dmodel, const SimArgs& a, int grid,
 struct KernelEntry {
   LaunchFn launch;
   const void* kernel;
+  int pool_words = 0;  // pool driver: 32-bit words of one trajectory's state record
 };
 
 // Thread-per-trajectory variants (kern_thread.cu, one object per precision x variant).
@@ -162,6 +176,19 @@ KernelEntry thread_seq_entry_fastocc_0();
 KernelEntry thread_seq_entry_fastocc_1();
 KernelEntry thread_seq_entry_fastocc_2();
 KernelEntry thread_seq_entry_fastocc_3();
+// Pool-driver builds (one per precision x variant; persistent form only).
+KernelEntry thread_pool_entry_ref_0();
+KernelEntry thread_pool_entry_ref_1();
+KernelEntry thread_pool_entry_ref_2();
+KernelEntry thread_pool_entry_ref_3();
+KernelEntry thread_pool_entry_fast_0();
+KernelEntry thread_pool_entry_fast_1();
+KernelEntry thread_pool_entry_fast_2();
+KernelEntry thread_pool_entry_fast_3();
+KernelEntry thread_pool_entry_fastocc_0();
+KernelEntry thread_pool_entry_fastocc_1();
+KernelEntry thread_pool_entry_fastocc_2();
+KernelEntry thread_pool_entry_fastocc_3();
 // Sequential driver with time-grid output (reference and fast builds).
 KernelEntry thread_seq_grid_entry_ref_0();
 KernelEntry thread_seq_grid_entry_ref_1();
@@ -191,8 +218,10 @@ struct NoAllocLaunch {
   int grid, block;
   SimArgs args;
 };
+#endif  // __CUDACC_RTC__
 }  // namespace mlk
 
+#ifndef __CUDACC_RTC__
 struct ml_model;
 namespace mlk {
 // Returns ML_OK and fills *out, or an ML_ERR_* code (message set).  `scratch_table_max`
@@ -207,3 +236,4 @@ int set_error(int code, const char* msg);
 bool is_device_pointer(const void* p);
 
 }  // namespace mlk
+#endif  // __CUDACC_RTC__

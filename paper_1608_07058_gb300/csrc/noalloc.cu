@@ -21,8 +21,8 @@ namespace {
 // loads the library holds these 4 KiB until the process exits.
 constexpr size_t kScratchBytes = 4096;
 constexpr size_t kTablesOffset = 256;
-// The largest one-trajectory-per-thread table set (8 species x 16 reactions) is 432 bytes.
-constexpr size_t kTableParamBytes = 512;
+// The largest one-trajectory-per-thread table set (8 species x 16 reactions) is 944 bytes.
+constexpr size_t kTableParamBytes = 1024;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 

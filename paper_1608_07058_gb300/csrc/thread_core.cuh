@@ -15,7 +15,9 @@
 //   explicit Poisson leap or implicit Newton leap (Rathinam 2003); one critical firing
 //   negativity check (halve tau1 and retry); commit x, r, G (trapezoid) and t.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
 #include "dev_common.cuh"
 #include "ml_internal.h"
@@ -247,11 +249,10 @@ __device__ __noinline__ PoissonDraw poisson_ptrs(typename P::R mu, uint32_t k0, 
 
 // Poisson(mu): 0 for mu <= 0 (no draw); inversion by sequential search below 10; PTRS.
 template <class P>
-__device__ __forceinline__ long long poisson_draw(typename P::R mu, uint32_t k0, uint32_t k1,
-                                                  uint32_t id, uint32_t step, uint32_t stream,
-                                                  uint32_t& status) {
+__device__ __forceinline__ PoissonDraw poisson_sample(typename P::R mu, uint32_t k0, uint32_t k1,
+                                                   uint32_t id, uint32_t step, uint32_t stream) {
   using R = typename P::R;
-  if (!(mu > R(0))) return 0;
+  if (!(mu > R(0))) return PoissonDraw{0, 0u};
   if (mu < R(10)) {
     const Words4 w = philox_block(k0, k1, id, step, stream, 0);
     const R u = P::u(w, 0);
@@ -264,19 +265,27 @@ __device__ __forceinline__ long long poisson_draw(typename P::R mu, uint32_t k0,
       if (p == R(0)) break;
       F = F + p;
     }
-    return k;
+    return PoissonDraw{k, 0u};
   }
-  const PoissonDraw d = (!P::kRef && mu > R(4.0e6))
-                            ? poisson_ptrs<PrecWide>((double)mu, k0, k1, id, step, stream)
-                            : poisson_ptrs<P>(mu, k0, k1, id, step, stream);
+  return (!P::kRef && mu > R(4.0e6)) ? poisson_ptrs<PrecWide>((double)mu, k0, k1, id, step, stream)
+                                     : poisson_ptrs<P>(mu, k0, k1, id, step, stream);
+}
+
+template <class P>
+__device__ __forceinline__ long long poisson_draw(typename P::R mu, uint32_t k0, uint32_t k1,
+                                                  uint32_t id, uint32_t step, uint32_t stream,
+                                                  uint32_t& status) {
+  const PoissonDraw d = poisson_sample<P>(mu, k0, k1, id, step, stream);
   status |= d.flags;
   return d.k;
 }
 
-template <int NM, int MM, class P>
+// MDL: the model tables' type -- the shared-memory ThreadModel staged at kernel start, or
+// a type with the same members known at compile time.
+template <int NM, int MM, class P, class MDL = ThreadModel<NM, MM>>
 struct ThreadTraj {
   using R = typename P::R;
-  using Model = ThreadModel<NM, MM>;
+  using Model = MDL;
 
   // g_j at an integer state (0 when some x_s < m_js), product in increasing s.
   __device__ static __forceinline__ R g_int(const Model& md, int j, const long long (&x)[NM]) {
@@ -291,6 +300,22 @@ struct ThreadTraj {
       }
     }
     return zero ? R(0) : v;
+  }
+
+  // Fast precision: g_j from an FP32 copy of the state (exact while counts stay below
+  // 2^24, where it equals g_int; above, FP32 rounds the count as g_int's conversion does).
+  __device__ static __forceinline__ float g_flt(const Model& md, int j, const float (&xf)[NM]) {
+    float v = 1.f;
+    bool zero = false;
+#pragma unroll
+    for (int s = 0; s < NM; ++s) {
+      const int m = md.ord[j][s];
+      if (m != 0) {
+        if (xf[s] < (float)m) zero = true;
+        else v = v * comb_factor<float>(xf[s], m);
+      }
+    }
+    return zero ? 0.f : v;
   }
 
   // g_j at a real state (implicit solve), FP64 always.
@@ -639,36 +664,66 @@ struct ThreadTraj {
 
   // Inverse-CDF pick of a reaction with probability v_j / sum v, from the second uniform
   // of block w (words 2, 3).  Reference: sequential prefix sums in index order (the
-  // canonical order), target u * sum with the lane-tree sum.  Fast: the same search over
-  // double-float prefix sums of the FP32 values with a 48-bit uniform, so reactions far
-  // below the total (propensities spanning many decades) keep their exact share without
-  // FP64 work.  Rounding that leaves no hit picks the last positive entry.
+  // canonical order), target u * sum with the lane-tree sum.  Fast: see pick_fast.
+  // Rounding that leaves no hit picks the last positive entry.
   __device__ static __forceinline__ int pick_reaction(const R (&v)[MM], const Words4& w) {
+    if (!P::kRef) return pick_fast(v, w);
     int pk = -1, last = -1;
-    if (P::kRef) {
-      const R target = P::u(w, 1) * lane_tree_sum<MM, R>(v);
-      R acc = R(0);
+    const R target = P::u(w, 1) * lane_tree_sum<MM, R>(v);
+    R acc = R(0);
 #pragma unroll
-      for (int j = 0; j < MM; ++j) {
-        if (v[j] > R(0)) last = j;
-        acc = acc + v[j];
-        if (pk < 0 && target < acc) pk = j;
-      }
-    } else {
-      // inclusive prefix sums once; the total is the last one
-      DF pre[MM];
-      DF acc{0.f, 0.f};
-#pragma unroll
-      for (int j = 0; j < MM; ++j) {
-        if (v[j] > R(0)) last = j;
-        acc = df_add(acc, (float)v[j]);
-        pre[j] = acc;
-      }
-      const DF target = df_uniform_times(acc, w.w2, w.w3);
-#pragma unroll
-      for (int j = 0; j < MM; ++j)
-        if (pk < 0 && df_lt(target, pre[j])) pk = j;
+    for (int j = 0; j < MM; ++j) {
+      if (v[j] > R(0)) last = j;
+      acc = acc + v[j];
+      if (pk < 0 && target < acc) pk = j;
     }
+    return pk < 0 ? last : pk;
+  }
+
+  // Fast precision pick with a 48-bit uniform u = (w2>>8) 2^-24 + ((w3>>8) + 1/2) 2^-48.
+  // First in FP32: prefix sums P_j and the target (w2>>8) 2^-24 P_{M-1}.  Against exact
+  // arithmetic each P_j is off by less than M 2^-24 P_{M-1} and the target by less than
+  // (M + 1) 2^-24 P_{M-1}, so when the target is farther than (M + 2) 2^-23 P_{M-1} from
+  // every P_j the FP32 search selects the reaction the exact one does.  Otherwise (about
+  // 2 M (M + 2) 2^-23 of the picks, ~1e-5) the double-float search decides, which keeps
+  // reactions many decades below the total at their exact share.
+  __device__ static __forceinline__ int pick_fast(const R (&v)[MM], const Words4& w) {
+    float pre[MM];
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      acc = acc + (float)v[j];
+      pre[j] = acc;
+    }
+    const float target = (float)(w.w2 >> 8) * 0x1p-24f * acc;
+    const float margin = (float)(MM + 2) * 0x1p-23f * acc;
+    int pk = 0;
+    bool clear = true;
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      pk += pre[j] <= target ? 1 : 0;
+      clear = clear && fabsf(pre[j] - target) > margin;
+    }
+    if (clear && pk < MM) return pk;
+    return pick_df(v, w);
+  }
+
+  // The same search over double-float (TwoSum) prefix sums of the FP32 values with the
+  // full 48-bit uniform; rarely taken, so kept out of line.
+  __device__ static __noinline__ int pick_df(const R (&v)[MM], const Words4& w) {
+    int pk = -1, last = -1;
+    DF pre[MM];
+    DF acc{0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      if (v[j] > R(0)) last = j;
+      acc = df_add(acc, (float)v[j]);
+      pre[j] = acc;
+    }
+    const DF target = df_uniform_times(acc, w.w2, w.w3);
+#pragma unroll
+    for (int j = 0; j < MM; ++j)
+      if (pk < 0 && df_lt(target, pre[j])) pk = j;
     return pk < 0 ? last : pk;
   }
 
@@ -694,12 +749,12 @@ struct ImplicitIo {
 // once per Jacobian entry and eliminated element: FP64 division is a long instruction
 // sequence on this GPU.  Not inlined: its FP64 working set stays out of the register
 // allocation of the leap loop.  Returns 0 converged, 1 not converged, 2 singular.
-template <int NM, int MM>
-__device__ __noinline__ int implicit_leap_wide(const ThreadModel<NM, MM>& md,
+template <int NM, int MM, class MDL>
+__device__ __noinline__ int implicit_leap_wide(const MDL& md,
                                                ImplicitIo<NM, MM>& io, uint32_t nc,
                                                double tau, double tol, int maxit, double fd_h,
                                                bool analytic) {
-  using TR = ThreadTraj<NM, MM, PrecRef>;
+  using TR = ThreadTraj<NM, MM, PrecRef, MDL>;
   double th[MM], ax[MM], y[NM], c[NM];
 #pragma unroll
   for (int j = 0; j < MM; ++j) {
@@ -835,11 +890,11 @@ __device__ __noinline__ int implicit_leap_wide(const ThreadModel<NM, MM>& md,
 
 // Fast precision, FP32 implicit leap for the increment z = y - x (ThreadTraj::
 // implicit_solve_fast), also not inlined.
-template <int NM, int MM>
-__device__ __noinline__ int implicit_leap_fp32(const ThreadModel<NM, MM>& md,
+template <int NM, int MM, class MDL>
+__device__ __noinline__ int implicit_leap_fp32(const MDL& md,
                                                ImplicitIo<NM, MM>& io, uint32_t nc, float tau,
                                                double tol, int maxit) {
-  using TF = ThreadTraj<NM, MM, PrecFast>;
+  using TF = ThreadTraj<NM, MM, PrecFast, MDL>;
   float th[MM];
   long long x[NM], K[MM];
 #pragma unroll
@@ -863,11 +918,11 @@ __device__ __noinline__ int implicit_leap_fp32(const ThreadModel<NM, MM>& md,
 // the sequential algorithm, so results do not depend on the schedule.
 // kGrid: time-grid output compiled in.  Without it the grid code is absent, so the
 // kernels that serve calls without a grid are exactly the plain simulation.
-template <int NM, int MM, class P, bool kGrid = false>
+template <int NM, int MM, class P, bool kGrid = false, class MDL = ThreadModel<NM, MM>>
 struct ThreadLane {
   using R = typename P::R;
-  using TT = ThreadTraj<NM, MM, P>;
-  using Model = ThreadModel<NM, MM>;
+  using TT = ThreadTraj<NM, MM, P, MDL>;
+  using Model = MDL;
   enum : int { kIdle = 0, kEval = 1, kSsa = 2, kDone = 3 };
 
   long long i;
@@ -989,6 +1044,76 @@ struct ThreadLane {
     mode = kIdle;
   }
 
+  // The lane state as 32-bit words of a shared-memory record (pool driver): word k of
+  // slot q at rec[k * kPoolSlots + q], the mode first.  g, a and a0 are not kept: a
+  // loaded lane recomputes them from x and theta before use.
+  static constexpr int kRWords = (int)(sizeof(R) / 4);
+  static constexpr int kWords = lane_record_words(NM, MM, kRWords == 2);
+  template <int S>
+  __device__ __forceinline__ void save(uint32_t* rec, int q) const {
+    int k = 0;
+    auto put = [&](uint32_t v) { rec[(k++) * S + q] = v; };
+    auto put64 = [&](unsigned long long v) {
+      put((uint32_t)v);
+      put((uint32_t)(v >> 32));
+    };
+    put((uint32_t)mode);
+    put(id);
+    put(status);
+    put(step);
+    put((uint32_t)reject_run);
+    put((uint32_t)b);
+    put((uint32_t)n_max);
+    put64((unsigned long long)i);
+    put64((unsigned long long)__double_as_longlong(t));
+    put64((unsigned long long)__double_as_longlong(T));
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      if constexpr (kRWords == 2) put64((unsigned long long)__double_as_longlong((double)th[j]));
+      else put(__float_as_uint((float)th[j]));
+    }
+#pragma unroll
+    for (int s2 = 0; s2 < NM; ++s2) put64((unsigned long long)x[s2]);
+#pragma unroll
+    for (int j = 0; j < MM; ++j) put64((unsigned long long)r[j]);
+#pragma unroll
+    for (int j = 0; j < MM; ++j) put64((unsigned long long)__double_as_longlong(G[j]));
+#pragma unroll
+    for (int c = 0; c < 4; ++c) put64((unsigned long long)cnt[c]);
+  }
+  template <int S>
+  __device__ __forceinline__ void load(const uint32_t* rec, int q) {
+    int k = 0;
+    auto get = [&]() { return rec[(k++) * S + q]; };
+    auto get64 = [&]() {
+      const unsigned long long lo = get();
+      return lo | ((unsigned long long)get() << 32);
+    };
+    mode = (int)get();
+    id = get();
+    status = get();
+    step = get();
+    reject_run = (int)get();
+    b = (int)get();
+    n_max = (int)get();
+    i = (long long)get64();
+    t = __longlong_as_double((long long)get64());
+    T = __longlong_as_double((long long)get64());
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      if constexpr (kRWords == 2) th[j] = (R)__longlong_as_double((long long)get64());
+      else th[j] = (R)__uint_as_float(get());
+    }
+#pragma unroll
+    for (int s2 = 0; s2 < NM; ++s2) x[s2] = (long long)get64();
+#pragma unroll
+    for (int j = 0; j < MM; ++j) r[j] = (long long)get64();
+#pragma unroll
+    for (int j = 0; j < MM; ++j) G[j] = __longlong_as_double((long long)get64());
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cnt[c] = (long long)get64();
+  }
+
   __device__ __forceinline__ void begin_burst(int n) {
     mode = kSsa;
     b = 0;
@@ -1002,29 +1127,53 @@ struct ThreadLane {
   }
 
   // Up to n_slice firings of the SSA burst (Gillespie 1977 direct method) at outer step
-  // `step`, firing index b; g, a, a0 are current for b == 0.  Fast precision accumulates
-  // the slice's G increments and elapsed time in compensated FP32 and folds them into
-  // the FP64 totals at the end of the slice.
-  __device__ __forceinline__ void ssa_slice(const Model& md, const SimArgs& A, int n_slice) {
+  // `step`, firing index b; g, a, a0 are current for b == 0 (or recomputed with fresh).
+  // Fast precision accumulates the slice's G increments in FP32 and its elapsed time in
+  // compensated FP32 and folds them into the FP64 totals at the end of the slice (every
+  // driver runs slices of kSsaPerRound firings, so all fold at the same firings).  The firing counts of the slice are kept in
+  // 32-bit registers and added to r once at the end.  The random block of the next
+  // firing is generated while the current one is processed: it depends only on the
+  // counter, so the two dependency chains overlap.
+  __device__ __forceinline__ void ssa_slice(const Model& md, const SimArgs& A, int n_slice,
+                                            bool fresh = false) {
     const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
     const uint32_t Mr = (uint32_t)A.M;
     const double rem = T - t;
     const float remf = (float)rem;
     float el = 0.f, elc = 0.f;
-    float Gs[MM], Gc[MM];
+    float Gs[MM];
+    int rc[MM];
 #pragma unroll
-    for (int j = 0; j < MM; ++j) Gs[j] = Gc[j] = 0.f;
+    for (int j = 0; j < MM; ++j) {
+      Gs[j] = 0.f;
+      rc[j] = 0;
+    }
+    // fast precision: an FP32 copy of the state, updated with the FP32 net changes, so
+    // that the propensities need no 64-bit conversions; synchronized at every slice start
+    float xf[NM];
+#pragma unroll
+    for (int s = 0; s < NM; ++s) xf[s] = P::kRef ? 0.f : (float)x[s];
+    const int b_first = b;
     bool to_horizon = false, burst_over = false;
+    Words4 w = philox_block(k0, k1, id, step, Mr + 2u, (uint32_t)b);
     for (int k = 0; k < n_slice; ++k) {
-      if (b > 0) {
-        TT::eval_props(md, x, th, g, a);
+      if (b > 0 || (fresh && k == 0)) {  // the state changed at the previous firing
+        if (P::kRef) {
+          TT::eval_props(md, x, th, g, a);
+        } else {
+#pragma unroll
+          for (int j = 0; j < MM; ++j) {
+            g[j] = (R)TT::g_flt(md, j, xf);
+            a[j] = th[j] * g[j];
+          }
+        }
         a0 = reaction_sum<MM, R, P::kRef>(a);
       }
       if (a0 == R(0)) {
         to_horizon = burst_over = true;
         break;
       }
-      const Words4 w = philox_block(k0, k1, id, step, Mr + 2u, (uint32_t)b);
+      const Words4 w_next = philox_block(k0, k1, id, step, Mr + 2u, (uint32_t)b + 1u);
       if (P::kRef) {
         const R dt = -P::log(P::u(w, 0)) / a0;
         const double tn = t + (double)dt;
@@ -1037,29 +1186,51 @@ struct ThreadLane {
         if (kGrid && A.K_obs > 0) record(A, tn, false);  // points before the firing: old state
         t = tn;
       } else {
-        const float dt = (float)(-P::log(P::u(w, 0)) / a0);
+        const float dt = __fdividef(-P::log(P::u(w, 0)), a0);  // about 2 ulp
         if ((el - elc) + dt > remf) {
           to_horizon = burst_over = true;
           break;
         }
+        // a slice holds at most kSsaPerRound firings: its G sums of that many positive
+        // terms are within 8 FP32 roundings; the elapsed time is summed compensated
 #pragma unroll
-        for (int j = 0; j < MM; ++j) kahan_add(Gs[j], Gc[j], (float)g[j] * dt);
+        for (int j = 0; j < MM; ++j) Gs[j] = fmaf((float)g[j], dt, Gs[j]);
         kahan_add(el, elc, dt);
         if (kGrid && A.K_obs > 0) record(A, t + ((double)el - (double)elc), false);
       }
       const int pick = TT::pick_reaction(a, w);
+      if constexpr (Model::kCompiled) {
+        // compile-time net changes: one predicated update per nonzero entry
 #pragma unroll
-      for (int s = 0; s < NM; ++s) x[s] += md.nu[pick][s];
+        for (int j = 0; j < MM; ++j) {
 #pragma unroll
-      for (int j = 0; j < MM; ++j) r[j] += (j == pick) ? 1 : 0;
-      cnt[2] += 1;
+          for (int s = 0; s < NM; ++s) {
+            if (md.nu[j][s] != 0 && j == pick) {
+              x[s] += md.nu[j][s];
+              if (!P::kRef) xf[s] += md.nuf[j][s];
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int s = 0; s < NM; ++s) {
+          x[s] += md.nu[pick][s];
+          if (!P::kRef) xf[s] += md.nuf[pick][s];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < MM; ++j) rc[j] += (j == pick) ? 1 : 0;
       if (kGrid && A.K_obs > 0)  // a point at the firing time: new state
         record(A, P::kRef ? t : t + ((double)el - (double)elc), true);
+      w = w_next;
       if (++b >= n_max) {
         burst_over = true;
         break;
       }
     }
+#pragma unroll
+    for (int j = 0; j < MM; ++j) r[j] += rc[j];
+    cnt[2] += b - b_first;
     if (P::kRef) {
       if (to_horizon) {
         const double rm = T - t;
@@ -1069,9 +1240,9 @@ struct ThreadLane {
       }
     } else {
       const double elapsed = (double)el - (double)elc;
-      // one FP64 addition per reaction and slice: the compensated FP32 sum rounded once
+      // one FP64 addition per reaction and slice
 #pragma unroll
-      for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)(Gs[j] - Gc[j]);
+      for (int j = 0; j < MM; ++j) G[j] = G[j] + (double)Gs[j];
       if (to_horizon) {
         const double left = rem - elapsed > 0.0 ? rem - elapsed : 0.0;
 #pragma unroll
@@ -1125,23 +1296,19 @@ struct ThreadLane {
     if (A.mode == ML_MODE_SSA_ONLY) {
       burst = A.n_ssa_ex;
     } else {
-      // critical reactions
+      // critical reactions: a_j > 0 and min over consumed species of floor(x_s/|nu_js|)
+      // below n_c, i.e. some consumed species has x_s < n_c |nu_js| (no division needed)
       uint32_t nc = 0;
       R ac[MM];
 #pragma unroll
       for (int j = 0; j < MM; ++j) {
         bool crit = false;
         if (a[j] > R(0)) {
-          long long L = -1;
 #pragma unroll
           for (int s = 0; s < NM; ++s) {
             const int v = md.nu[j][s];
-            if (v < 0) {
-              const long long l = (v == -1) ? x[s] : x[s] / (long long)(-v);
-              if (L < 0 || l < L) L = l;
-            }
+            if (v < 0 && x[s] < (long long)A.n_c * (long long)(-v)) crit = true;
           }
-          crit = (L >= 0 && L < (long long)A.n_c);
         }
         if (!crit) nc |= 1u << j;
         ac[j] = crit ? a[j] : R(0);
@@ -1338,10 +1505,128 @@ struct ThreadLane {
 // or 8 lanes need one, measured 2.6 and 1.8 times slower on the gene-expression batch.)
 constexpr int kSsaPerRound = 8;
 
-// Kernel: stage the model tables once per CTA, then run the lane state machine.  Plain
-// form (queue null): thread i runs trajectory i.  Persistent form: lanes claim trajectory
-// indices from the device queue (in the caller's order, if any) and refill as soon as
-// their trajectory ends.
+// Round-based driver: plain form (queue null): thread i runs trajectory i.  Persistent
+// form: lanes claim trajectory indices from the device queue (in the caller's order, if
+// any) and refill as soon as their trajectory ends.
+template <int NM, int MM, class P, class MDL>
+__device__ __forceinline__ void run_rounds(const MDL& md, bool staged, const SimArgs& args) {
+  using Lane = ThreadLane<NM, MM, P, false, MDL>;
+  Lane L;
+  L.mode = Lane::kIdle;
+  const long long first = args.queue ? queue_claim(args.queue, args.order, args.n_traj)
+                                     : (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (first < args.n_traj) L.start(md, args, first);
+  for (;;) {
+    if (L.mode == Lane::kDone) {
+      L.finish(args, staged);
+      if (args.queue) {
+        const long long nxt = queue_claim(args.queue, args.order, args.n_traj);
+        if (nxt < args.n_traj) L.start(md, args, nxt);
+      }
+    }
+    if (!__any_sync(0xffffffffu, L.mode != Lane::kIdle)) break;
+    if (L.mode == Lane::kEval) {
+      L.eval_phase(md, args);
+    } else if (L.mode == Lane::kSsa) {
+      L.ssa_slice(md, args, kSsaPerRound);
+    }
+  }
+}
+
+// Pool driver: every warp keeps kPoolSlots trajectories (two per lane) in shared memory
+// and in each round runs one phase for 32 of them: SSA slices while at least 32 (or more
+// than the evaluations waiting) are inside a burst, else leap evaluations.  A lane loads
+// the chosen trajectory's state, runs the phase and stores it back, so the lanes of a
+// warp execute the same phase instead of taking turns between the evaluation and the SSA
+// code (the round-based driver's lanes diverge there).  A finished trajectory is written
+// out and its slot refilled from the work queue at once.  Persistent form only.
+
+// Position of the (n+1)-th set bit of m (n < popcount(m)).
+__device__ __forceinline__ int nth_set_bit(unsigned long long m, int n) {
+  const uint32_t lo = (uint32_t)m, hi = (uint32_t)(m >> 32);
+  const int clo = __popc(lo);
+  uint32_t v = n < clo ? lo : hi;
+  int k = n < clo ? n : n - clo;
+  for (; k > 0; --k) v &= v - 1u;
+  return (n < clo ? 0 : 32) + __ffs((int)v) - 1;
+}
+
+template <int NM, int MM, class P, class MDL>
+__device__ __forceinline__ void run_pool(const MDL& md, bool staged, const SimArgs& args,
+                                         uint32_t* pool_words) {
+  using Lane = ThreadLane<NM, MM, P, false, MDL>;
+  const int lane = threadIdx.x & 31;
+  uint32_t* rec = pool_words + (size_t)(threadIdx.x >> 5) * Lane::kWords * kPoolSlots;
+#pragma unroll 1
+  for (int h = lane; h < kPoolSlots; h += 32) {
+    Lane L;
+    L.mode = Lane::kIdle;
+    const long long idx = queue_claim(args.queue, args.order, args.n_traj);
+    if (idx < args.n_traj) L.start(md, args, idx);
+    L.template save<kPoolSlots>(rec, h);
+  }
+  __syncwarp();
+  // the search for ready slots starts at a rotating position, so that no slot waits
+  // while others are served round after round
+  int rot = 0;
+  for (;;) {
+    const uint32_t m_lo = rec[lane], m_hi = rec[32 + lane];  // mode words
+    const unsigned long long ms =
+        (unsigned long long)__ballot_sync(0xffffffffu, m_lo == (uint32_t)Lane::kSsa) |
+        ((unsigned long long)__ballot_sync(0xffffffffu, m_hi == (uint32_t)Lane::kSsa) << 32);
+    const unsigned long long me =
+        (unsigned long long)__ballot_sync(0xffffffffu, m_lo == (uint32_t)Lane::kEval) |
+        ((unsigned long long)__ballot_sync(0xffffffffu, m_hi == (uint32_t)Lane::kEval) << 32);
+    const int ns = __popcll(ms), ne = __popcll(me);
+    if (ns + ne == 0) break;
+    const bool ssa = ns >= 32 || (ne < 32 && ns >= ne);
+    const int n_run = ssa ? ns : ne;
+    const unsigned long long m = ssa ? ms : me;
+    const int r0 = rot;
+    rot = (rot + 29) & (kPoolSlots - 1);
+    const unsigned long long mr = r0 ? (m >> r0) | (m << (kPoolSlots - r0)) : m;
+    if (lane < n_run) {
+      const int q = (nth_set_bit(mr, lane) + r0) & (kPoolSlots - 1);
+      Lane L;
+      L.template load<kPoolSlots>(rec, q);
+      if (ssa) L.ssa_slice(md, args, kSsaPerRound, true);
+      else L.eval_phase(md, args);
+      if (L.mode == Lane::kDone) {
+        L.finish(args, staged);
+        const long long nxt = queue_claim(args.queue, args.order, args.n_traj);
+        if (nxt < args.n_traj) L.start(md, args, nxt);
+      }
+      L.template save<kPoolSlots>(rec, q);
+    }
+    __syncwarp();
+  }
+}
+
+// Sequential per-lane driver over the same lane state machine: each thread runs its
+// trajectory to the end before claiming the next one.  It has less scheduling overhead
+// and suits leap-dominated workloads; the autotuner picks between the drivers.  Its kGrid
+// build serves every thread-shape call with time-grid output (the drivers give identical
+// results).
+template <int NM, int MM, class P, bool kGrid, class MDL>
+__device__ __forceinline__ void run_sequential(const MDL& md, bool staged, const SimArgs& args) {
+  using Lane = ThreadLane<NM, MM, P, kGrid, MDL>;
+  Lane L;
+  long long i = args.queue ? queue_claim(args.queue, args.order, args.n_traj)
+                           : (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  while (i < args.n_traj) {
+    L.start(md, args, i);
+    while (L.mode != Lane::kDone) {
+      if (L.mode == Lane::kEval) L.eval_phase(md, args);
+      else L.ssa_slice(md, args, kSsaPerRound);
+    }
+    L.finish(args, staged);
+    if (!args.queue) break;
+    i = queue_claim(args.queue, args.order, args.n_traj);
+  }
+}
+
+// Kernels over the run-time tables: stage the model once per CTA into shared memory (one
+// bulk copy), then run a driver.
 template <int NM, int MM, class P>
 __global__ void ML_THREAD_BOUNDS k_thread(const ThreadModel<NM, MM>* __restrict__ gmd,
                                           const SimArgs args) {
@@ -1349,34 +1634,20 @@ __global__ void ML_THREAD_BOUNDS k_thread(const ThreadModel<NM, MM>* __restrict_
   __shared__ uint64_t mbar;
   const bool staged = stage_model_bulk(&smd, gmd, (uint32_t)thread_model_bytes<NM, MM>(), &mbar,
                                        args.stage_polls);
-  using Lane = ThreadLane<NM, MM, P>;
-  Lane L;
-  L.mode = Lane::kIdle;
-  const long long first = args.queue ? queue_claim(args.queue, args.order, args.n_traj)
-                                     : (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (first < args.n_traj) L.start(smd, args, first);
-  for (;;) {
-    if (L.mode == Lane::kDone) {
-      L.finish(args, staged);
-      if (args.queue) {
-        const long long nxt = queue_claim(args.queue, args.order, args.n_traj);
-        if (nxt < args.n_traj) L.start(smd, args, nxt);
-      }
-    }
-    if (!__any_sync(0xffffffffu, L.mode != Lane::kIdle)) break;
-    if (L.mode == Lane::kEval) {
-      L.eval_phase(smd, args);
-    } else if (L.mode == Lane::kSsa) {
-      L.ssa_slice(smd, args, kSsaPerRound);
-    }
-  }
+  run_rounds<NM, MM, P>(smd, staged, args);
 }
 
-// Sequential per-lane driver over the same lane state machine: each thread runs its
-// trajectory to the end (whole SSA bursts at once) before claiming the next one.  It has
-// less scheduling overhead and suits leap-dominated workloads; the autotuner picks between
-// the two drivers.  Its kGrid build serves every thread-shape call with time-grid output
-// (the two drivers give identical results).
+template <int NM, int MM, class P>
+__global__ void ML_THREAD_BOUNDS k_thread_pool(const ThreadModel<NM, MM>* __restrict__ gmd,
+                                               const SimArgs args) {
+  __shared__ ThreadModel<NM, MM> smd;
+  __shared__ uint64_t mbar;
+  extern __shared__ uint32_t pool_words[];
+  const bool staged = stage_model_bulk(&smd, gmd, (uint32_t)thread_model_bytes<NM, MM>(), &mbar,
+                                       args.stage_polls);
+  run_pool<NM, MM, P>(smd, staged, args, pool_words);
+}
+
 template <int NM, int MM, class P, bool kGrid = false>
 __global__ void ML_THREAD_BOUNDS k_thread_seq(const ThreadModel<NM, MM>* __restrict__ gmd,
                                               const SimArgs args) {
@@ -1384,20 +1655,7 @@ __global__ void ML_THREAD_BOUNDS k_thread_seq(const ThreadModel<NM, MM>* __restr
   __shared__ uint64_t mbar;
   const bool staged = stage_model_bulk(&smd, gmd, (uint32_t)thread_model_bytes<NM, MM>(), &mbar,
                                        args.stage_polls);
-  using Lane = ThreadLane<NM, MM, P, kGrid>;
-  Lane L;
-  long long i = args.queue ? queue_claim(args.queue, args.order, args.n_traj)
-                           : (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  while (i < args.n_traj) {
-    L.start(smd, args, i);
-    while (L.mode != Lane::kDone) {
-      if (L.mode == Lane::kEval) L.eval_phase(smd, args);
-      else L.ssa_slice(smd, args, 0x7fffffff);
-    }
-    L.finish(args, staged);
-    if (!args.queue) break;
-    i = queue_claim(args.queue, args.order, args.n_traj);
-  }
+  run_sequential<NM, MM, P, kGrid>(smd, staged, args);
 }
 
 }  // namespace mlk

@@ -46,7 +46,7 @@ class ml_sim_params(C.Structure):
                 ("shape", C.c_int32), ("block_size", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("use_graph", C.c_int32), ("jacobian", C.c_int32),
                 ("newton_precision", C.c_int32), ("stage_poll_limit", C.c_int32),
-                ("queue_order", C.c_void_p)]
+                ("queue_order", C.c_void_p), ("specialize", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -101,7 +101,10 @@ def test_simulate_rejects_bad_params(ml):
     x0 = torch.zeros(1, dtype=torch.int64)
     T = torch.ones(1, dtype=torch.float64)
     for kw in ({"eps": 0.0}, {"eps": 1.5}, {"n_ssa_explicit": 0}, {"mode": 7}, {"precision": 3},
-               {"block_size": 48}, {"newton_maxit": 0}):
+               {"block_size": 48}, {"newton_maxit": 0}, {"specialize": 2},
+               {"shape": ml.ML_SHAPE_THREAD_POOL},  # the pool driver needs the persistent form
+               {"shape": ml.ML_SHAPE_THREAD_POOL_OCC, "form": ml.ML_FORM_PERSISTENT},  # fast only
+               {"shape": 8}):
         with pytest.raises(ml.MatleapError) as e:
             ml.ml_simulate(m, 4, x0, T, params=ml.ml_default_params(**kw))
         assert e.value.code == ml.ML_ERR_ARG
