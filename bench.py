@@ -171,10 +171,28 @@ POISSON_PTRS_OPS = 110
 NEWTON_ITERATIONS = 4.3  # mean iterations per implicit leap on dimerisation states (oracle)
 
 # Per-launch figures measured by ncu for the headline kernel, keyed by (config, shape,
-# threads per CTA) of the launch the bench times: DRAM bytes read + written, warp
-# instructions issued and FP64-pipe busy fraction, with the capture they come from (a
-# profiles/ summary).  A launch shape without a capture of the current kernel reports null.
-PROFILED = {}
+# threads per CTA, specialized) of the launch the bench times: DRAM bytes read + written,
+# warp instructions issued and FP64-pipe instruction rate (of peak), with the capture they
+# come from (a profiles/ summary).  A launch shape without a capture of the current kernel
+# reports null.  Captures: the full 1,000,000-trajectory batch, one launch each, CTAs per
+# SM by occupancy.
+_SRC = ("ncu --metrics gpu__time_duration.sum,smsp__inst_executed.sum,dram__bytes_read.sum,"
+        "dram__bytes_write.sum,sm__inst_executed_pipe_fp64... -k regex:ml_jit -s 1 -c 1 "
+        "python bench.py --config 2 --steps 1 --warmup 1 --no-plain --no-cpu "
+        "--serving-seconds 0 --ncu --shape S --block B "
+        "(profiles/k_jit_pool_fast_gene_expression_1M.md)")
+PROFILED = {
+    (2, 6, 128, 1): {"dram_bytes": 262120960 + 209241088, "warp_inst": 123710711486,
+                     "fp64_pipe_pct": 31.60, "source": _SRC},
+    (2, 6, 256, 1): {"dram_bytes": 263632640 + 209561856, "warp_inst": 123667242930,
+                     "fp64_pipe_pct": 31.62, "source": _SRC},
+    (2, 6, 64, 1): {"dram_bytes": 265054208 + 209970688, "warp_inst": 123713090021,
+                    "fp64_pipe_pct": 31.53, "source": _SRC},
+    (2, 1, 256, 1): {"dram_bytes": 271331584 + 210071040, "warp_inst": 188576129640,
+                     "fp64_pipe_pct": 41.24, "source": _SRC},
+    (2, 7, 64, 1): {"dram_bytes": 280494336 + 1490402048, "warp_inst": 135008423302,
+                    "fp64_pipe_pct": 35.65, "source": _SRC},
+}
 
 
 def work_model(crn):
@@ -309,7 +327,8 @@ def run_serving(ml, seconds, rate_hz=200.0, seed=11, max_inflight=8, budget=8 <<
     reqs = W.serving_requests(n_req, seed=seed, rate_hz=rate_hz)
     models = {m: ml.model_from_crn(W.config(m, n_traj=1).crn) for m in (0, 1, 2, 3)}
     params = ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32, form=ml.ML_FORM_PERSISTENT,
-                                  max_steps=MAX_STEPS, jacobian=ml.ML_JAC_ANALYTIC)
+                                  max_steps=MAX_STEPS, jacobian=ml.ML_JAC_ANALYTIC,
+                                  specialize=1)
     total_traj = sum(q["workload"].n_traj for q in reqs)
 
     # one request per launch, in arrival order: measured service times, queueing by the
@@ -604,6 +623,7 @@ class Bench:
         evs, launches = [], 0
         self.barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed launches
         t0 = time.perf_counter()
         k = 0
         while k < steps:
@@ -622,6 +642,7 @@ class Bench:
                 if time.perf_counter() - t0 > budget_s:
                     break
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         self.barrier()
         wall = time.perf_counter() - t0
         ms = [a.elapsed_time(b) for a, b in evs]
@@ -691,11 +712,11 @@ def run_ours(args):
         theta = None if w.theta is None else torch.as_tensor(w.theta, device=dev)
         return w, model, x0, T, theta
 
-    def tune(model, B, x0, T, theta, p):
+    def tune(model, B, x0, T, theta, p, n_sample=100_000):
         if args.shape:
             p.shape, p.block_size, p.ctas_per_sm = args.shape, args.block, 0
         elif not args.ncu and not args.no_autotune:
-            best = ml.ml_autotune(model, B, x0, T, theta, params=p, n_sample=min(B, 100_000))
+            best = ml.ml_autotune(model, B, x0, T, theta, params=p, n_sample=min(B, n_sample))
             p.shape, p.block_size, p.ctas_per_sm = best.shape, best.block_size, best.ctas_per_sm
         return p
 
@@ -711,7 +732,19 @@ def run_ours(args):
     # weak scaling: rank k simulates ids [k B, (k+1) B) of a world x B batch
     id_base, _ = ml.shard_bounds(world * B, rank, world)
     stage(f"headline workload {workload_name(w)}: autotune ...")
-    fast = tune(model, B, x0, T, theta, fast_params())
+    # the headline batch is tuned as a whole, in the longest-first order of a pilot run
+    # with another seed: a prefix under-fills the GPU differently (the pool driver keeps 64
+    # trajectories per warp) and its tail is not the batch's
+    p0 = fast_params()
+    if not args.no_order and not args.shape and not args.ncu and not args.no_autotune:
+        pilot = ml.ml_simulate(model, B, x0, T, theta, params=p0, seed=999,
+                               traj_id_base=id_base)
+        c = pilot["counters"]
+        pilot_order = torch.argsort(8 * (c[:, 0] + c[:, 1]) + c[:, 2] + c[:, 3], descending=True,
+                                    stable=True).to(torch.int64).contiguous()
+        p0.queue_order = pilot_order.data_ptr()
+    fast = tune(model, B, x0, T, theta, p0, n_sample=B)
+    fast.queue_order = None
     stage(f"headline: shape {int(fast.shape)}, block {int(fast.block_size)}; timing ...")
     clocks = ClockSampler(local)
     if not args.ncu:
@@ -771,7 +804,8 @@ def run_ours(args):
     peak_clock = 2070.0
     peak = sms * 128 * peak_clock * 1e6 / 1e12   # Tops/s: SMs x 4 schedulers x 32 lanes x clock
     achieved = ops_per_launch / (ms_fast / 1e3) / 1e12
-    prof = PROFILED.get((args.config, int(fast.shape), int(fast.block_size)), {}) \
+    prof = PROFILED.get((args.config, int(fast.shape), int(fast.block_size),
+                         int(fast.specialize)), {}) \
         if (args.n_traj is None and args.horizon is None) else {}
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                         "frac": achieved / peak, "traffic": prof.get("dram_bytes"),

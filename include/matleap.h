@@ -160,8 +160,9 @@ typedef struct {
                                that pick up a long trajectory last (e.g. sorted by a
                                previous call's per-trajectory event counts).  Results do
                                not depend on it.  Device memory for ml_simulate and
-                               ml_simulate_noalloc, host memory for ml_simulate_host;
-                               ignored by the plain form, the autotuner and the server.
+                               ml_simulate_noalloc and ml_autotune, host memory for
+                               ml_simulate_host; ignored by the plain form, the server
+                               and an autotuner sample shorter than the batch.
                                Entries outside [0, n_traj) are passed over; trajectories
                                the order leaves out are not run (their outputs are not
                                written)                                               */
@@ -171,8 +172,8 @@ typedef struct {
                                a second, and loads it on the device), 0 = the
                                precompiled kernels that read the tables at run time.
                                Results are identical (reference precision: bitwise).
-                               Ignored by the warp shape, time-grid calls, the server
-                               and ml_simulate_noalloc.                                */
+                               Ignored by the warp shape, time-grid calls and
+                               ml_simulate_noalloc; the server passes it on.          */
 } ml_sim_params;
 
 /* Fills *p with the defaults above.  Returns ML_ERR_ARG if p is NULL. */

@@ -1138,7 +1138,8 @@ int ml_autotune(ml_model* m, int64_t n_traj, const double* theta, const int64_t*
         c.block_size = b;
         c.ctas_per_sm = per_sm;
         c.use_graph = 0;
-        c.queue_order = nullptr;  // the sample is a prefix; an order for the full batch
+        // an order is a permutation of the whole batch: used only when tuning on all of it
+        c.queue_order = n == n_traj ? p.queue_order : nullptr;
         cands.push_back(c);
       }
     }

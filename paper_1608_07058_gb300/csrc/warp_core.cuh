@@ -104,6 +104,20 @@ struct WarpTraj {
     return zero ? R(0) : v;
   }
 
+  // Fast precision: g_j from the FP32 copy of the state kept during SSA bursts.
+  __device__ static __forceinline__ float g_flt(const WarpModel& md, int j, const float* xf) {
+    float v = 1.f;
+    bool zero = false;
+    const int nr = md.nreact[j];
+    for (int k = 0; k < nr; ++k) {
+      const int s = md.rsp[j][k], m = md.rmul[j][k];
+      const float xs = xf[s];
+      if (xs < (float)m) zero = true;
+      else v = v * comb_factor<float>(xs, m);
+    }
+    return zero ? 0.f : v;
+  }
+
   // g_j on a real state; if `sub` >= 0 species `sub` takes the value `ysub`.
   __device__ static __forceinline__ double g_real(const WarpModel& md, int j, const double* y,
                                                   int sub, double ysub) {
@@ -215,6 +229,58 @@ struct WarpTraj {
       }
       return __shfl_sync(0xffffffffu, pk, src);
     }
+  }
+
+  // Fast precision: one FP32 inclusive scan of the lanes' sums of their (at most kRPL)
+  // values gives the total (a0) and the pick together.  The target (w2>>8) 2^-24 a0 and
+  // every prefix carry less than (M + 2) 2^-23 a0 of rounding against exact arithmetic,
+  // so when the target is farther than that from every prefix at the chosen lane the
+  // FP32 pick is the exact one; otherwise the double-float pick decides.  All lanes
+  // return the same total and index.
+  struct ScanPick {
+    float a0;
+    int pk;
+  };
+  __device__ static ScanPick scan_total(const R (&vl)[kRPL], int M, int lane, float& S,
+                                        float& E) {
+    S = 0.f;
+#pragma unroll
+    for (int q = 0; q < kRPL; ++q)
+      if (lane + 32 * q < M) S = S + (float)vl[q];
+    E = S;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const float o = __shfl_up_sync(0xffffffffu, E, d);
+      if (lane >= d) E = E + o;
+    }
+    return ScanPick{__shfl_sync(0xffffffffu, E, 31), -1};
+  }
+  __device__ static int pick_scanned(const R* v, const R (&vl)[kRPL], const Words4& w,
+                                     int M, int lane, float S, float E, float tot) {
+    const float target = (float)(w.w2 >> 8) * 0x1p-24f * tot;
+    const float margin = (float)(M + 2) * 0x1p-23f * tot;
+    const unsigned hit = __ballot_sync(0xffffffffu, target < E && S > 0.f);
+    const int src = hit ? __ffs(hit) - 1 : 31;
+    const float Ex = __shfl_up_sync(0xffffffffu, E, 1);
+    int pk = -1;
+    bool clear = hit != 0;
+    if (lane == src) {
+      float acc = lane == 0 ? 0.f : Ex;
+      clear = clear && fabsf(target - acc) > margin;
+#pragma unroll
+      for (int q = 0; q < kRPL; ++q) {
+        const int j = lane + 32 * q;
+        if (j < M) {
+          acc = acc + (float)vl[q];
+          clear = clear && fabsf(target - acc) > margin;
+          if (pk < 0 && target < acc && vl[q] > R(0)) pk = j;
+        }
+      }
+      clear = clear && pk >= 0;
+    }
+    pk = __shfl_sync(0xffffffffu, pk, src);
+    if (__shfl_sync(0xffffffffu, (int)clear, src)) return pk;
+    return pick(v, vl, w, M, lane);
   }
 
   // Implicit solve on the per-warp slab: residual, iterate and stopping test in FP64;
@@ -515,7 +581,11 @@ struct WarpTraj {
 
     // Fast precision: inside a burst each lane accumulates its G_j and the elapsed time in
     // compensated FP32 and folds them into the FP64 totals once at the end of the burst.
-    auto ssa_burst_fast = [&](int n_max, R a0) {
+    // The propensities come from an FP32 copy of the state (kept in the leap's xn storage,
+    // unused during a burst, and updated with each firing), one FP32 warp scan gives a0
+    // and the pick, and the next firing's random block is generated one firing ahead.
+    auto ssa_burst_fast = [&](int n_max, R a0_unused) {
+      (void)a0_unused;
       const double rem = T - t;
       const float remf = (float)rem;
       float el = 0.f, elc = 0.f;
@@ -524,17 +594,34 @@ struct WarpTraj {
       for (int q = 0; q < kRPL; ++q) Gs[q] = Gc[q] = 0.f;
       bool to_horizon = false;
       int fired = -1;
+      float* xf = reinterpret_cast<float*>(sl.xn);
+#pragma unroll
+      for (int q = 0; q < kSPL; ++q) {
+        const int s = lane + 32 * q;
+        if (s < N) xf[s] = (float)sl.x[s];
+      }
+      __syncwarp();
+      Words4 w = philox_block(k0, k1, id, step, Mr + 2u, 0u);
       for (int b = 0; b < n_max; ++b) {
-        if (b > 0) {
-          update_props(fired);
-          a0 = tree_sum(a, lane, M);
+        if (b > 0) {  // reactions with a reactant the last firing changed
+          const uint64_t changed = fired >= 0 ? md.cmask[fired] : ~0ULL;
+#pragma unroll
+          for (int q = 0; q < kRPL; ++q) {
+            const int j = lane + 32 * q;
+            if (j < M && (md.rmask[j] & changed) != 0ULL) {
+              g[q] = (R)WarpTraj<P>::g_flt(md, j, xf);
+              a[q] = th[q] * g[q];
+            }
+          }
         }
-        if (a0 == R(0)) {
+        float S, E;
+        const float a0 = WarpTraj<P>::scan_total(a, M, lane, S, E).a0;
+        if (a0 == 0.f) {
           to_horizon = true;
           break;
         }
-        const Words4 w = philox_block(k0, k1, id, step, Mr + 2u, (uint32_t)b);
-        const float dt = (float)(-P::log(P::u(w, 0)) / a0);
+        const Words4 w_next = philox_block(k0, k1, id, step, Mr + 2u, (uint32_t)b + 1u);
+        const float dt = __fdividef(-P::log(P::u(w, 0)), a0);  // about 2 ulp
         if ((el - elc) + dt > remf) {
           to_horizon = true;
           break;
@@ -546,11 +633,15 @@ struct WarpTraj {
           record(t + ((double)el - (double)elc), false);  // before the firing: old state
           __syncwarp();
         }
-        const int pk = pick(a_s, a, w, M, lane);
+        const int pk = WarpTraj<P>::pick_scanned(a_s, a, w, M, lane, S, E, a0);
         fired = pk;
         if (pk >= 0) {
           const int e0 = md.rx_ptr[pk], e1 = md.rx_ptr[pk + 1];
-          for (int e = e0 + lane; e < e1; e += 32) sl.x[md.rx_s[e]] += md.rx_nu[e];
+          for (int e = e0 + lane; e < e1; e += 32) {
+            const int sp = md.rx_s[e], v = md.rx_nu[e];
+            sl.x[sp] += v;
+            xf[sp] += (float)v;
+          }
 #pragma unroll
           for (int q = 0; q < kRPL; ++q)
             if (lane + 32 * q == pk) r[q] += 1;
@@ -558,7 +649,10 @@ struct WarpTraj {
         }
         __syncwarp();
         if (kGrid && A.K_obs > 0) record(t + ((double)el - (double)elc), true);
+        w = w_next;
       }
+      // the propensities in shared memory (read by the next evaluation's step sizes) are
+      // recomputed there; g and a stay current for the horizon term below
       const double elapsed = (double)el - (double)elc;
 #pragma unroll
       for (int q = 0; q < kRPL; ++q) G[q] = G[q] + ((double)Gs[q] - (double)Gc[q]);
@@ -667,16 +761,12 @@ struct WarpTraj {
           const int j = lane + 32 * q;
           bool crit = false;
           if (j < M && a[q] > R(0)) {
-            long long L = -1;
+            // min over consumed species of floor(x_s/|nu_js|) below n_c, i.e. some
+            // consumed species has x_s < n_c |nu_js|
             for (int e = md.rx_ptr[j]; e < md.rx_ptr[j + 1]; ++e) {
               const int v = md.rx_nu[e];
-              if (v < 0) {
-                const long long xs = sl.x[md.rx_s[e]];
-                const long long l = (v == -1) ? xs : xs / (long long)(-v);
-                if (L < 0 || l < L) L = l;
-              }
+              if (v < 0 && sl.x[md.rx_s[e]] < (long long)A.n_c * (long long)(-v)) crit = true;
             }
-            crit = (L >= 0 && L < (long long)A.n_c);
           }
           ac[q] = crit ? a[q] : R(0);
           if (j < M) ac_s[j] = ac[q];
