@@ -89,6 +89,9 @@ def parse():
     ap.add_argument("--no-order", action="store_true",
                     help="hand trajectories out in index order (no longest-first queue order)")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--plain-n-traj", type=int, default=None,
+                    help="time the plain FP64 form on this prefix of the batch (slow workloads)")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--generic", action="store_true",
                     help="batched form on the precompiled kernels (no model-specialized kernels)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -777,13 +780,19 @@ def run_ours(args):
                                   "rejected_leaps": float(counts_fast[3])},
             "gpu_launches": int(res_fast["launches"])}
 
-    def plain_leg(model, B, x0, T, theta, crn, seed0, budget_s):
+    def plain_leg(model, B, x0, T, theta, crn, seed0, budget_s, n_sub=None):
+        # n_sub: time the plain form on a prefix of the batch (its rate is per trajectory)
+        if n_sub is not None and n_sub < B:
+            x0 = x0 if x0.dim() == 1 else x0[:n_sub]
+            T = T if T.numel() == 1 else T[:n_sub]
+            theta = None if theta is None else theta[:n_sub]
+            B = n_sub
         res = bench.timed(model, B, x0, T, theta, plain_params(crn), seed0, id_base,
                                   args.steps, 0, budget_s=budget_s)
         msp = max_over_ranks(res["mean_ms"])
         cnt = sum_over_ranks(res["counts"].astype(np.float64)) / res["steps"]
         return {"value": world * B / (msp / 1e3), "unit": "trajectories/s", "ms_per_step": msp,
-                "steps": res["steps"],
+                "steps": res["steps"], "trajectories_per_step": B,
                 "warmup": "one untimed launch on a 4,096-trajectory prefix",
                 "leap_steps_per_s": float(cnt[:3].sum()) / (msp / 1e3),
                 "gpu_launches": int(res["launches"]),
@@ -792,7 +801,8 @@ def run_ours(args):
 
     if not args.no_plain:
         guarded(line, "plain_fp64",
-                lambda: plain_leg(model, B, x0, T, theta, w.crn, 5000, args.plain_budget_s))
+                lambda: plain_leg(model, B, x0, T, theta, w.crn, 5000, args.plain_budget_s,
+                                  args.plain_n_traj))
         if "value" in line["plain_fp64"]:
             line["batched_vs_plain"] = line["value"] / line["plain_fp64"]["value"]
 
@@ -862,7 +872,7 @@ def run_ours(args):
             e2e["h2d_bytes_per_step"] += B * 8
         return e2e
 
-    if not args.ncu:
+    if not args.ncu and not args.no_e2e:
         dev_order = fast.queue_order
         try:
             guarded(line, "e2e", e2e_leg)

@@ -2,10 +2,12 @@
 that hold at any size and on sampled trajectory ids against the oracle.
 
 - Gene expression, 1,000,000 trajectories in the launch configuration the benchmark times
-  (fast precision, persistent form, CUDA graph, autotuned shape): X(T) = x0 + nu^T r
-  exactly and nothing negative on all of them; the ensemble statistics of 3,000 ids spread
-  over the batch agree with the oracle run on the same ids (4-SE mean and variance, KS,
-  Holm at 0.01).
+  (fast precision, persistent form, CUDA graph, kernels compiled for the model, pool
+  driver -- the shape the benchmark's whole-batch autotuning picks on GB300): X(T) =
+  x0 + nu^T r exactly and nothing negative on all of them; the ensemble statistics of
+  3,000 ids spread over the batch agree with the oracle run on the same ids (4-SE mean and
+  variance, KS, Holm at 0.01).  The same launch in reference precision: 200 ids spread
+  over the batch bit-identical to the oracle.
 - Random 50 x 100 network, its full batch of 65,536 trajectories (one per warp) over a
   short horizon, reference precision: the same invariants on all, and 64 sampled ids
   bit-identical to the oracle."""
@@ -60,7 +62,8 @@ def test_gene_expression_full_batch_fast(ml, oracle):
     w = W.config(2)
     assert w.n_traj == 1_000_000
     p = ml.ml_default_params(precision=ml.ML_PREC_FAST_FP32, form=ml.ML_FORM_PERSISTENT,
-                             use_graph=1, max_steps=MAX_STEPS)
+                             use_graph=1, max_steps=MAX_STEPS, specialize=1,
+                             shape=ml.ML_SHAPE_THREAD_POOL, block_size=128)
     g = _device_run(ml, w, w.T, p, seed=77)
     _invariants(w, g)
     assert (g["status"] & ~np.uint32(2 | 8) == 0).all()
@@ -76,6 +79,21 @@ def test_gene_expression_full_batch_fast(ml, oracle):
     sub = {k: g[k][ids] for k in ("X", "r", "G")}
     s = stats_util.summary(stats_util.compare(sub, o, g_res=stats_util.G_RESOLUTION_FAST))
     assert s["holm_pass_0.01"], s
+
+
+def test_gene_expression_full_batch_ref_specialized_sampled(ml, oracle):
+    w = W.config(2)
+    p = ml.ml_default_params(form=ml.ML_FORM_PERSISTENT, use_graph=1, max_steps=MAX_STEPS,
+                             specialize=1, shape=ml.ML_SHAPE_THREAD_POOL, block_size=128)
+    g = _device_run(ml, w, w.T, p, seed=78)
+    _invariants(w, g)
+    ids = np.unique(np.concatenate([np.linspace(0, w.n_traj - 1, 199).astype(np.int64),
+                                    [w.n_traj - 1]]))
+    for i in ids:
+        oi = oracle.simulate(w.crn, 1, w.x0, w.T[i:i + 1], w.theta[i:i + 1],
+                             params=oracle.Params(max_steps=MAX_STEPS), seed=78,
+                             traj_id_base=int(i))
+        assert_bit_parity({k: v[i:i + 1] for k, v in g.items()}, oi, f"id {i}")
 
 
 def test_random_crn_full_batch_ref_sampled(ml, oracle):
