@@ -10,7 +10,8 @@ workload (0 immigration-death, 1 stiff dimerisation, 3 random 50 x 100 network).
 A step is one simulate call over the whole batch.  Two forms are timed:
   batched  fast precision (FP32 propensities, step sizes, Poisson means and G
            increments; FP64 time, G totals and implicit Newton solve), persistent refill
-           kernel launched from a CUDA graph, autotuned shape  -> the headline `value`;
+           kernel compiled for the model at run time, launched from a CUDA graph, shape
+           autotuned on the whole batch  -> the headline `value`;
   plain    reference precision (FP64 everywhere), one launch, one thread per trajectory
            (`plain_fp64`, timed for at most --plain-budget-s seconds, at least 2 steps).
 Inputs are resident in HBM when timing starts; a 256 MB buffer is written between steps to
