@@ -911,11 +911,13 @@ __device__ __noinline__ int implicit_leap_fp32(const MDL& md,
 }
 
 // One trajectory per thread, driven as a per-lane state machine so that a warp does not
-// hold lanes in one phase while others run a long phase: in each round a lane performs
-// either one leap evaluation (propensities, critical set, step sizes, leap or burst
-// decision) or a bounded slice of its SSA burst.  Finished lanes refill from the work
-// queue inside the loop (persistent form).  Each lane performs exactly the arithmetic of
-// the sequential algorithm, so results do not depend on the schedule.
+// hold lanes in one phase while others run a long phase: a step of the machine is either
+// one leap evaluation (propensities, critical set, step sizes, leap or burst decision) or
+// a bounded slice of the SSA burst.  The drivers below (round-based, pool, sequential)
+// only decide which lane runs which step when; each lane performs exactly the arithmetic
+// of the sequential algorithm, so results do not depend on the schedule.  MDL: the model
+// tables read at run time (ThreadModel in shared memory) or compiled in (specialized
+// kernels).
 // kGrid: time-grid output compiled in.  Without it the grid code is absent, so the
 // kernels that serve calls without a grid are exactly the plain simulation.
 template <int NM, int MM, class P, bool kGrid = false, class MDL = ThreadModel<NM, MM>>
