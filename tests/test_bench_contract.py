@@ -25,3 +25,24 @@ def test_reference_arm_json_line():
     assert d["cpu_single_core"]["cores"] == 1 and d["cpu_single_core"]["value"] > 0
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_profiled_counters_name_launch_shapes_and_their_capture():
+    """The ncu figures the headline line reports (roofline.traffic, roofline.issue) are
+    keyed by launch shapes the library has, and cite a committed profile summary; the DRAM
+    traffic of a launch cannot be below its algorithmic inputs and outputs."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1608_07058_gb300 import workloads as W
+    shapes = set(bench.SHAPE_NAMES)
+    for (cfg, shape, block, spec), v in bench.PROFILED.items():
+        assert cfg in (0, 1, 2, 3) and shape in shapes and block in (64, 128, 256)
+        assert spec in (0, 1)
+        w = W.config(cfg, n_traj=1)
+        B = W.config(cfg).n_traj
+        N, M = w.crn.n_species, w.crn.n_reactions
+        algorithmic = B * (8 * N + 16 * M + 36) + B * 8 * M + B * 8  # as the line computes
+        assert v["dram_bytes"] >= algorithmic * 0.9, (cfg, shape, block)
+        assert v["warp_inst"] > 0 and 0.0 <= v["fp64_pipe_pct"] <= 100.0
+        ref = v["source"].split("profiles/")[1].rstrip(")")
+        assert os.path.exists(os.path.join(ROOT, "profiles", ref)), ref
