@@ -237,12 +237,9 @@ struct WarpTraj {
   // so when the target is farther than that from every prefix at the chosen lane the
   // FP32 pick is the exact one; otherwise the double-float pick decides.  All lanes
   // return the same total and index.
-  struct ScanPick {
-    float a0;
-    int pk;
-  };
-  __device__ static ScanPick scan_total(const R (&vl)[kRPL], int M, int lane, float& S,
-                                        float& E) {
+  // Returns the total; S = the lane's own sum, E = the inclusive prefix at the lane.
+  __device__ static float scan_total(const R (&vl)[kRPL], int M, int lane, float& S,
+                                     float& E) {
     S = 0.f;
 #pragma unroll
     for (int q = 0; q < kRPL; ++q)
@@ -253,7 +250,7 @@ struct WarpTraj {
       const float o = __shfl_up_sync(0xffffffffu, E, d);
       if (lane >= d) E = E + o;
     }
-    return ScanPick{__shfl_sync(0xffffffffu, E, 31), -1};
+    return __shfl_sync(0xffffffffu, E, 31);
   }
   __device__ static int pick_scanned(const R* v, const R (&vl)[kRPL], const Words4& w,
                                      int M, int lane, float S, float E, float tot) {
@@ -615,7 +612,7 @@ struct WarpTraj {
           }
         }
         float S, E;
-        const float a0 = WarpTraj<P>::scan_total(a, M, lane, S, E).a0;
+        const float a0 = WarpTraj<P>::scan_total(a, M, lane, S, E);
         if (a0 == 0.f) {
           to_horizon = true;
           break;
