@@ -69,8 +69,44 @@ def test_tau_second_order_hor_factor(oracle):
     b = 0.03 * 100 / h
     want = min(b / (2 * a), b * b / (4 * a))
     assert abs(oracle.tau_select(crn, [a], [100, 0]) - want) < 1e-15 * want
-    # below two molecules the fractional term is dropped: bound = max(0.03/2, 1) = 1
-    assert abs(oracle.tau_select(crn, [0.0], [1, 0]) - math.inf) == 0 or True
+    # below two molecules the reaction cannot fire: no change expected, no bound
+    assert math.isinf(oracle.tau_select(crn, [0.0], [1, 0]))
+
+
+def test_tau_third_order_hor_factors(oracle):
+    """Cao 2006's highest-order factors of third-order reactions, on hand values:
+    3A: 3 + 1/(x-1) + 2/(x-2); 2A + B: 1.5 (2 + 1/(x_A-1)) for A and 3 for B;
+    A + B + C: 3 for each."""
+    eps = 0.03
+    # 3A -> B at x = 1000: a = k C(1000, 3), mu_A = -3a, var_A = 9a, bound eps x / h
+    crn = W._crn("tri", 2, [({0: 3}, {1: 1}, 1e-7)])
+    a = 1e-7 * 1000 * 999 * 998 / 6
+    h = (3.0 + 1.0 / 999.0) + 2.0 / 998.0
+    b = eps * 1000 / h
+    want = min(b / (3 * a), b * b / (9 * a))
+    assert abs(oracle.tau_select(crn, [a], [1000, 0]) - want) < 1e-15 * want
+    # at x = 50 the bound eps x / h < 1 is raised to one molecule
+    a = 1e-7 * 50 * 49 * 48 / 6
+    assert abs(oracle.tau_select(crn, [a], [50, 0]) - min(1 / (3 * a), 1 / (9 * a))) < 1e-15 / a
+    # 2A + B -> C at (40, 30): A: h = 1.5 (2 + 1/39), mu = -2a, var = 4a; B: h = 3, mu = -a
+    crn = W._crn("dimb", 3, [({0: 2, 1: 1}, {2: 1}, 1e-4)])
+    a = 1e-4 * (40 * 39 / 2) * 30
+    hA, hB = 1.5 * (2.0 + 1.0 / 39.0), 3.0
+    bA, bB = max(eps * 40 / hA, 1.0), max(eps * 30 / hB, 1.0)
+    want = min(bA / (2 * a), bA * bA / (4 * a), bB / a, bB * bB / a)
+    assert abs(oracle.tau_select(crn, [a], [40, 30, 0]) - want) < 1e-15 * want
+    crn = W._crn("dimb", 3, [({0: 2, 1: 1}, {2: 1}, 1e-8)])
+    a = 1e-8 * (4000 * 3999 / 2) * 3000
+    hA = 1.5 * (2.0 + 1.0 / 3999.0)
+    bA, bB = eps * 4000 / hA, eps * 3000 / 3.0
+    want = min(bA / (2 * a), bA * bA / (4 * a), bB / a, bB * bB / a)
+    assert abs(oracle.tau_select(crn, [a], [4000, 3000, 0]) - want) < 1e-15 * want
+    # A + B + C -> D at (2000, 3000, 4000): h = 3 for each, mu = -a, var = a
+    crn = W._crn("abc", 4, [({0: 1, 1: 1, 2: 1}, {3: 1}, 1e-9)])
+    a = 1e-9 * 2000 * 3000 * 4000
+    want = min(min(eps * x / 3 / a, (eps * x / 3) ** 2 / a) for x in (2000, 3000, 4000))
+    assert abs(oracle.tau_select(crn, [a], [2000, 3000, 4000, 0]) - want) < 1e-15 * want
+    assert abs(want - 20.0 / 24.0) < 1e-12  # species A decides: bound 20 over a = 24
 
 
 def test_implicit_solve_linear_network_matches_linear_solve(oracle):
